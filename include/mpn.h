@@ -1,0 +1,201 @@
+/*
+ * mpn -- max-pooling path planner on GB300 (sm_103a). C ABI.
+ *
+ * The method (arXiv 2004.00540, "Generation of Paths in a Maze using a Deep
+ * Network without Learning"): a stack of identical layers, each a 3x3
+ * stride-1 max pool followed by adding the environment map I_e (0 free,
+ * -maxint obstacle) and the source map I_s, then a ReLU (Methods, "Activity
+ * Map Generation", Fig. 1). Activity spreads one cell per layer from the
+ * sources; the layer at which a free cell first turns positive is its
+ * 8-connected unit-cost hop distance d to the nearest source, and the final
+ * activity map is O = L + 1 - d on reached cells. A path is read back from any
+ * start by stepping to the neighbour with the largest activity, i.e. distance
+ * d - 1 (Methods, "Path Reconstruction").
+ *
+ * Vocabulary: the paper calls the cells where activity starts "sources"; this
+ * API calls them TARGETS (the cells paths lead to). Paths are traced from
+ * STARTS. Cells are addressed by linear index y * W + x (row-major).
+ *
+ * Conventions for every call:
+ *  - Every call returns an mpn_status; nothing aborts or exits.
+ *  - Pointer arguments documented "host or device" are classified with
+ *    cudaPointerGetAttributes: device (and managed) memory is read in place,
+ *    anything else is treated as host memory and copied.
+ *  - Work is ordered on the context's stream (mpn_create's stream, or
+ *    mpn_set_stream). A context is not thread-safe; separate contexts are
+ *    independent. The caller owns every buffer it passes; the context owns
+ *    the resident mask, distance plane and scratch until mpn_destroy.
+ *  - Calls that do not need a host-visible result return before the GPU work
+ *    finishes. An error the GPU detects (layer cap, distance overflow, a wait
+ *    that timed out) is reported by the next call that synchronises
+ *    (mpn_sync, mpn_get_distances, mpn_trace*, mpn_get_stats, or
+ *    mpn_propagate with a non-NULL layers_run).
+ */
+#ifndef MPN_H
+#define MPN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpn_ctx mpn_ctx;
+
+typedef enum {
+    MPN_OK = 0,
+    MPN_EINVAL = 1,     /* bad argument: sizes < 1, index out of range, no targets */
+    MPN_ENOMEM = 2,     /* device allocation failed, or an output capacity too small */
+    MPN_ECUDA = 3,      /* a CUDA runtime call failed */
+    MPN_ETIMEOUT = 4,   /* a grid-wide wait ran past its iteration limit */
+    MPN_EOVERFLOW = 5,  /* a distance does not fit the uint16 plane */
+    MPN_EOBSTACLE = 6,  /* a target lies on an obstacle */
+    MPN_ESTATE = 7      /* call out of order (trace before propagate) */
+} mpn_status;
+
+/* distance plane element type */
+#define MPN_DIST_AUTO 0   /* uint16 if H*W <= 65535, else uint32 */
+#define MPN_DIST_U16 16
+#define MPN_DIST_U32 32
+/* unreached cells and obstacles hold the all-ones sentinel of the dtype */
+#define MPN_UNREACHED16 0xFFFFu
+#define MPN_UNREACHED32 0xFFFFFFFFu
+
+/* per-start trace status */
+#define MPN_PATH_OK 0
+#define MPN_PATH_UNREACHABLE 1
+#define MPN_PATH_ON_OBSTACLE 2
+
+/*
+ * Create a context for one H x W grid and encode its mask (Methods, "Input":
+ * the environment map I_e). mask: H*W uint8, row-major, nonzero = obstacle,
+ * host or device. dist_bits: MPN_DIST_AUTO / _U16 / _U32. stream: a
+ * cudaStream_t (NULL = legacy default stream). Allocates all device memory
+ * the grid needs (mask bits, visit bits, distance plane, tile flags).
+ * H, W >= 1 and H*W < 2^32 - 1, else MPN_EINVAL.
+ */
+mpn_status mpn_create(const uint8_t *mask, int32_t H, int32_t W, int32_t dist_bits,
+                      void *stream, mpn_ctx **out);
+
+/*
+ * Like mpn_create, from an already packed FREE-cell bit plane: H rows of
+ * pitch_words uint32 words; bit b of word w in row y is cell x = 32*w + b,
+ * 1 = free. pitch_words >= ceil(W/32); bits at x >= W are ignored. Host or
+ * device.
+ */
+mpn_status mpn_create_packed(const uint32_t *free_bits, int32_t H, int32_t W,
+                             int32_t pitch_words, int32_t dist_bits, void *stream,
+                             mpn_ctx **out);
+
+/* Re-encode a new H*W uint8 mask of the same size (host or device), keeping
+ * all allocations. Invalidates earlier distances. */
+mpn_status mpn_set_mask(mpn_ctx *ctx, const uint8_t *mask);
+
+/* Bind later work to another stream (a cudaStream_t). */
+mpn_status mpn_set_stream(mpn_ctx *ctx, void *stream);
+
+/*
+ * Propagate activity from the targets (Methods, "Activity Map Generation";
+ * the paper's I_s holds 1 at each target) and write the distance plane.
+ * targets: n_targets >= 1 linear indices (uint32), host or device;
+ * duplicates allowed. A target out of range gives MPN_EINVAL, one on an
+ * obstacle MPN_EOBSTACLE (the paper's formula would make it a dead source).
+ * max_layers = 0 runs until a layer activates no new cell (Methods,
+ * "Determining the number of layers L", read as "stop at the first layer that
+ * adds nothing"); max_layers = L > 0 is the paper's fixed-depth network of L
+ * layers: cells with d > L stay unreached. layers_run (host, may be NULL):
+ * receives the largest finite distance; passing it makes the call wait for
+ * the GPU and report its errors.
+ */
+mpn_status mpn_propagate(mpn_ctx *ctx, const uint32_t *targets, int32_t n_targets,
+                         uint32_t max_layers, uint32_t *layers_run);
+
+/*
+ * Same result as mpn_propagate, computed the way the paper's recursive mode
+ * runs (Appendix, Table I: one layer per iteration): one kernel launch per
+ * layer over the whole distance plane, with the host reading a "did anything
+ * change" flag every check_every layers (>= 1). Baseline only.
+ */
+mpn_status mpn_propagate_plain(mpn_ctx *ctx, const uint32_t *targets, int32_t n_targets,
+                               uint32_t max_layers, int32_t check_every,
+                               uint32_t *layers_run);
+
+/* Copy the distance plane (H*W elements of the context's dtype, row-major)
+ * to dst; dst_on_device selects cudaMemcpyDeviceToDevice vs DeviceToHost.
+ * Waits for the copy. MPN_ESTATE before the first propagate. */
+mpn_status mpn_get_distances(mpn_ctx *ctx, void *dst, int32_t dst_on_device);
+
+/*
+ * The paper's final activity map O after L layers (Methods, "Activity Map
+ * Generation"): O = L + 1 - d where d <= L, 0 elsewhere (obstacles,
+ * unreached, farther than L). dst: H*W int32, device or host
+ * (dst_on_device). L = 0 means the layer count of the last propagate.
+ */
+mpn_status mpn_get_activity(mpn_ctx *ctx, uint32_t L, int32_t *dst, int32_t dst_on_device);
+
+/*
+ * Path lengths only (for sizing): offsets[0] = 0 and offsets[i+1] -
+ * offsets[i] = d(start_i) + 1 cells for a reachable start, 0 otherwise.
+ * starts: n >= 0 uint32 linear indices, host or device. offsets: n+1 uint64,
+ * host. Waits for the GPU.
+ */
+mpn_status mpn_trace_lengths(mpn_ctx *ctx, const uint32_t *starts, int32_t n,
+                             uint64_t *offsets);
+
+/*
+ * Simple path reconstruction (Methods, "Path Reconstruction") from every
+ * start: start first, then repeatedly the 8-neighbour with distance d - 1 --
+ * among several, the one with the lowest linear index (the paper picks at
+ * random) -- until a target (d = 0). Output in CSR form, host or device
+ * buffers:
+ *   offsets[n+1] uint64, cells[offsets[n]] uint32, status[n] int8
+ *   (MPN_PATH_OK / _UNREACHABLE / _ON_OBSTACLE; empty path unless OK).
+ * If offsets[n] > cells_cap, offsets and status are still written and the
+ * call returns MPN_ENOMEM so the caller can resize. A start index out of
+ * range is MPN_EINVAL. MPN_ESTATE before the first propagate. Waits for the
+ * GPU once (to size the output).
+ */
+mpn_status mpn_trace(mpn_ctx *ctx, const uint32_t *starts, int32_t n, uint64_t *offsets,
+                     uint32_t *cells, uint64_t cells_cap, int8_t *status);
+
+/* Wait for the context's stream; report any error the GPU recorded. */
+mpn_status mpn_sync(mpn_ctx *ctx);
+
+void mpn_destroy(mpn_ctx *ctx);
+
+const char *mpn_status_str(mpn_status s);
+
+/*
+ * Propagation tiling. variant: index into the compiled tile shapes
+ * (mpn_variant_info); depth: temporal blocking depth k = layers advanced per
+ * tile visit, 1..32 (also the halo width in rows). variant < 0 restores the
+ * automatic choice.
+ */
+mpn_status mpn_set_tuning(mpn_ctx *ctx, int32_t variant, int32_t depth);
+
+/* Shape of compiled tile variant v: region rows, region words (32 cells
+ * each), threads per block. MPN_EINVAL past the last variant. */
+mpn_status mpn_variant_info(int32_t v, int32_t *region_rows, int32_t *region_words,
+                            int32_t *threads);
+
+typedef struct {
+    int32_t H, W, pitch_words, dist_bits;
+    int32_t variant, depth;          /* tiling in use */
+    int32_t tiles_x, tiles_y, blocks;
+    uint32_t layers;                 /* largest finite distance of the last propagate */
+    uint32_t sweeps;                 /* grid-wide rounds of the last propagate */
+    uint64_t tile_visits;            /* tile visits of the last propagate */
+    float ms_encode, ms_propagate, ms_trace;   /* device time of the last call of each */
+} mpn_stats;
+
+/* Statistics of the last calls (waits for the GPU). */
+mpn_status mpn_get_stats(mpn_ctx *ctx, mpn_stats *out);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t mpn_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPN_H */

@@ -1,0 +1,585 @@
+// C ABI of the max-pooling path planner: context, device memory, staging of
+// host arguments, stream ordering and error reporting. Every entry point is
+// declared and documented in include/mpn.h.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "mpn_internal.cuh"
+
+using namespace mpn;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+constexpr uint32_t kSpinLimit = 1u << 24;   // ~ seconds of 100 ns polls
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want) {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mpn_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return MPN_OK;
+    if (e == cudaErrorMemoryAllocation) return MPN_ENOMEM;
+    return MPN_ECUDA;
+}
+
+mpn_status from_err_bits(uint32_t e) {
+    if (!e) return MPN_OK;
+    if (e & ERR_INVAL) return MPN_EINVAL;
+    if (e & ERR_OBSTACLE) return MPN_EOBSTACLE;
+    if (e & ERR_OVERFLOW) return MPN_EOVERFLOW;
+    if (e & (ERR_TIMEOUT | ERR_SWEEPS)) return MPN_ETIMEOUT;
+    return MPN_ECUDA;
+}
+
+#define MPN_TRY(expr)                                   \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) return from_cuda(e_);    \
+    } while (0)
+
+}  // namespace
+
+namespace mpn {
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+}  // namespace mpn
+
+struct mpn_ctx {
+    int H = 0, W = 0, P = 0, dist_bits = 32;
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+
+    DevBuf free_bits, vis, nb0, nb1, dist, ctl, tiles, mask_stage;
+    DevBuf targets, starts, offsets, status, cells, activity;
+
+    int variant = 0, depth = 32;
+    bool auto_tune = true;
+    int ntx = 0, nty = 0, TY = 0, TXW = 0, blocks = 0;
+
+    bool propagated = false;
+    uint32_t last_layers = 0, last_max_layers = 0;
+    bool stats_pending = false;
+    Ctl last_ctl{};
+
+    cudaEvent_t ev[6] = {};   // encode begin/end, propagate begin/end, trace begin/end
+    float ms_encode = 0.f, ms_propagate = 0.f, ms_trace = 0.f;
+    bool ev_enc = false, ev_prop = false, ev_trace = false;
+
+    GridDev grid() const {
+        GridDev g;
+        g.free_bits = (const uint32_t *)free_bits.p;
+        g.vis = (uint32_t *)vis.p;
+        g.nb0 = (uint32_t *)nb0.p;
+        g.nb1 = (uint32_t *)nb1.p;
+        g.dist = dist.p;
+        g.H = H;
+        g.W = W;
+        g.P = P;
+        return g;
+    }
+    size_t plane_words() const { return (size_t)H * P; }
+    size_t dist_bytes() const { return (size_t)H * W * (dist_bits / 8); }
+};
+
+namespace {
+
+// Tile geometry and grid size for (variant, depth); allocates the tile queue
+// (a stamp per tile and three tile lists).
+mpn_status configure(mpn_ctx *c, int variant, int depth) {
+    if (variant < 0 || variant >= num_variants()) return MPN_EINVAL;
+    const VariantDesc vd = variant_desc(variant);
+    const int ry = vd.nwarps * (32 / vd.rxw) * vd.r;
+    if (depth < 1 || depth > 32 || ry - 2 * depth < 1) return MPN_EINVAL;
+    const int TY = ry - 2 * depth, TXW = vd.rxw - 2;
+    const int wwords = (c->W + 31) / 32;
+    const int ntx = (wwords + TXW - 1) / TXW, nty = (c->H + TY - 1) / TY;
+    int bps = 0;
+    MPN_TRY(propagate_blocks_per_sm(variant, c->dist_bits, &bps));
+    if (bps < 1) return MPN_ECUDA;
+    const long long ntiles = (long long)ntx * nty;
+    long long blocks = (long long)bps * c->sm_count;
+    if (blocks > ntiles) blocks = ntiles;
+    if (blocks < 1) blocks = 1;
+    MPN_TRY(c->tiles.ensure((size_t)ntiles * 4 * sizeof(uint32_t)));
+    c->variant = variant;
+    c->depth = depth;
+    c->TY = TY;
+    c->TXW = TXW;
+    c->ntx = ntx;
+    c->nty = nty;
+    c->blocks = (int)blocks;
+    return MPN_OK;
+}
+
+// Default tiling: the 256 x 256-cell region (192-cell interior), depth 32.
+mpn_status auto_configure(mpn_ctx *c) { return configure(c, 0, 32); }
+
+mpn_status alloc_planes(mpn_ctx *c) {
+    const size_t pw = c->plane_words() * sizeof(uint32_t);
+    MPN_TRY(c->free_bits.ensure(pw));
+    MPN_TRY(c->vis.ensure(pw));
+    MPN_TRY(c->nb0.ensure(pw));
+    MPN_TRY(c->nb1.ensure(pw));
+    MPN_TRY(c->dist.ensure(c->dist_bytes()));
+    MPN_TRY(c->ctl.ensure(sizeof(Ctl)));
+    for (auto &e : c->ev) MPN_TRY(cudaEventCreate(&e));
+    return auto_configure(c);
+}
+
+mpn_status new_ctx(int32_t H, int32_t W, int32_t dist_bits, void *stream, mpn_ctx **out) {
+    if (!out) return MPN_EINVAL;
+    *out = nullptr;
+    if (H < 1 || W < 1 || (uint64_t)H * (uint64_t)W >= 0xffffffffull) return MPN_EINVAL;
+    if (dist_bits == MPN_DIST_AUTO) dist_bits = ((int64_t)H * W <= 65535) ? 16 : 32;
+    if (dist_bits != 16 && dist_bits != 32) return MPN_EINVAL;
+    mpn_ctx *c = new (std::nothrow) mpn_ctx();
+    if (!c) return MPN_ENOMEM;
+    c->H = H;
+    c->W = W;
+    c->P = (((W + 31) / 32) + 3) / 4 * 4;
+    c->dist_bits = dist_bits;
+    c->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return from_cuda(e);
+    }
+    mpn_status st = alloc_planes(c);
+    if (st != MPN_OK) {
+        mpn_destroy(c);
+        return st;
+    }
+    *out = c;
+    return MPN_OK;
+}
+
+// Copy n uint32 values to a device staging buffer unless already on device.
+mpn_status stage_u32(mpn_ctx *c, DevBuf &buf, const uint32_t *src, int32_t n,
+                     const uint32_t **dev) {
+    if (n <= 0) {
+        *dev = nullptr;
+        return MPN_OK;
+    }
+    if (is_device_ptr(src)) {
+        *dev = src;
+        return MPN_OK;
+    }
+    MPN_TRY(buf.ensure((size_t)n * sizeof(uint32_t)));
+    MPN_TRY(cudaMemcpyAsync(buf.p, src, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                            c->stream));
+    *dev = (const uint32_t *)buf.p;
+    return MPN_OK;
+}
+
+mpn_status encode_mask(mpn_ctx *c, const uint8_t *mask) {
+    if (!mask) return MPN_EINVAL;
+    const uint8_t *dm = mask;
+    MPN_TRY(cudaEventRecord(c->ev[0], c->stream));
+    if (!is_device_ptr(mask)) {
+        const size_t n = (size_t)c->H * c->W;
+        MPN_TRY(c->mask_stage.ensure(n));
+        MPN_TRY(cudaMemcpyAsync(c->mask_stage.p, mask, n, cudaMemcpyHostToDevice, c->stream));
+        dm = (const uint8_t *)c->mask_stage.p;
+    }
+    MPN_TRY(launch_pack(dm, c->H, c->W, c->P, (uint32_t *)c->free_bits.p, c->stream));
+    MPN_TRY(cudaEventRecord(c->ev[1], c->stream));
+    c->ev_enc = true;
+    c->propagated = false;
+    return MPN_OK;
+}
+
+// Collect the device-side result of the last propagate (waits).
+mpn_status finish_propagate(mpn_ctx *c) {
+    if (!c->stats_pending) return MPN_OK;
+    MPN_TRY(cudaMemcpyAsync(&c->last_ctl, c->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                            c->stream));
+    MPN_TRY(cudaStreamSynchronize(c->stream));
+    c->stats_pending = false;
+    c->last_layers = c->last_ctl.max_layer;
+    if (c->last_ctl.err) {
+        c->propagated = false;
+        return from_err_bits(c->last_ctl.err);
+    }
+    return MPN_OK;
+}
+
+mpn_status begin_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n,
+                           const uint32_t **dt) {
+    if (!c) return MPN_EINVAL;
+    if (!targets || n < 1) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);   // drain an earlier run's error report
+    (void)st;
+    c->propagated = false;
+    if (!is_device_ptr(targets)) {
+        const uint64_t N = (uint64_t)c->H * c->W;
+        for (int32_t i = 0; i < n; ++i)
+            if ((uint64_t)targets[i] >= N) return MPN_EINVAL;
+    }
+    st = stage_u32(c, c->targets, targets, n, dt);
+    if (st != MPN_OK) return st;
+    MPN_TRY(cudaMemsetAsync(c->dist.p, 0xff, c->dist_bytes(), c->stream));
+    MPN_TRY(cudaMemsetAsync(c->vis.p, 0, c->plane_words() * 4, c->stream));
+    MPN_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Ctl), c->stream));
+    return MPN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mpn_status_str(mpn_status s) {
+    switch (s) {
+        case MPN_OK: return "ok";
+        case MPN_EINVAL: return "invalid argument";
+        case MPN_ENOMEM: return "out of memory or output capacity too small";
+        case MPN_ECUDA: return "CUDA runtime error";
+        case MPN_ETIMEOUT: return "grid-wide wait timed out";
+        case MPN_EOVERFLOW: return "distance does not fit the uint16 plane";
+        case MPN_EOBSTACLE: return "target on an obstacle";
+        case MPN_ESTATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+uint64_t mpn_launch_count(void) { return g_launches.load(); }
+
+mpn_status mpn_create(const uint8_t *mask, int32_t H, int32_t W, int32_t dist_bits, void *stream,
+                      mpn_ctx **out) {
+    if (!mask) return MPN_EINVAL;
+    mpn_status st = new_ctx(H, W, dist_bits, stream, out);
+    if (st != MPN_OK) return st;
+    st = encode_mask(*out, mask);
+    if (st != MPN_OK) {
+        mpn_destroy(*out);
+        *out = nullptr;
+    }
+    return st;
+}
+
+mpn_status mpn_create_packed(const uint32_t *bits, int32_t H, int32_t W, int32_t pitch_words,
+                             int32_t dist_bits, void *stream, mpn_ctx **out) {
+    if (!bits || pitch_words < (W + 31) / 32) return MPN_EINVAL;
+    mpn_status st = new_ctx(H, W, dist_bits, stream, out);
+    if (st != MPN_OK) return st;
+    mpn_ctx *c = *out;
+    const uint32_t *src = bits;
+    DevBuf tmp;
+    cudaError_t e = cudaSuccess;
+    if (!is_device_ptr(bits)) {
+        const size_t bytes = (size_t)H * pitch_words * 4;
+        e = tmp.ensure(bytes);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tmp.p, bits, bytes, cudaMemcpyHostToDevice, c->stream);
+        src = (const uint32_t *)tmp.p;
+    }
+    if (e == cudaSuccess) e = launch_repack(src, H, W, pitch_words, c->P, (uint32_t *)c->free_bits.p, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    tmp.release();
+    if (e != cudaSuccess) {
+        mpn_destroy(c);
+        *out = nullptr;
+        return from_cuda(e);
+    }
+    return MPN_OK;
+}
+
+mpn_status mpn_set_mask(mpn_ctx *c, const uint8_t *mask) {
+    if (!c) return MPN_EINVAL;
+    finish_propagate(c);
+    return encode_mask(c, mask);
+}
+
+mpn_status mpn_set_stream(mpn_ctx *c, void *stream) {
+    if (!c) return MPN_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return MPN_OK;
+}
+
+mpn_status mpn_set_tuning(mpn_ctx *c, int32_t variant, int32_t depth) {
+    if (!c) return MPN_EINVAL;
+    if (variant < 0) {
+        c->auto_tune = true;
+        return auto_configure(c);
+    }
+    mpn_status st = configure(c, variant, depth);
+    if (st == MPN_OK) c->auto_tune = false;
+    return st;
+}
+
+mpn_status mpn_variant_info(int32_t v, int32_t *rows, int32_t *words, int32_t *threads) {
+    if (v < 0 || v >= num_variants()) return MPN_EINVAL;
+    const VariantDesc d = variant_desc(v);
+    if (rows) *rows = d.nwarps * (32 / d.rxw) * d.r;
+    if (words) *words = d.rxw;
+    if (threads) *threads = d.nwarps * 32;
+    return MPN_OK;
+}
+
+mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_t max_layers,
+                         uint32_t *layers_run) {
+    const uint32_t *dt = nullptr;
+    mpn_status st = begin_propagate(c, targets, n, &dt);
+    if (st != MPN_OK) return st;
+    const size_t ntiles = (size_t)c->ntx * c->nty;
+    MPN_TRY(cudaMemsetAsync(c->nb0.p, 0, c->plane_words() * 4, c->stream));
+    MPN_TRY(cudaMemsetAsync(c->nb1.p, 0, c->plane_words() * 4, c->stream));
+    MPN_TRY(cudaMemsetAsync(c->tiles.p, 0, ntiles * sizeof(uint32_t), c->stream));
+    PropParams p{};
+    p.g = c->grid();
+    p.queued = (uint32_t *)c->tiles.p;
+    p.lists = p.queued + ntiles;
+    p.ctl = (Ctl *)c->ctl.p;
+    p.ntx = c->ntx;
+    p.nty = c->nty;
+    p.k = c->depth;
+    p.TY = c->TY;
+    p.TXW = c->TXW;
+    p.max_layers = max_layers;
+    p.spin_limit = kSpinLimit;
+    const uint64_t bound = (max_layers ? (uint64_t)max_layers : (uint64_t)c->H * c->W) / c->depth + 3;
+    p.sweep_cap = (uint32_t)(bound < (1u << 22) ? bound : (1u << 22));
+    MPN_TRY(cudaEventRecord(c->ev[2], c->stream));
+    MPN_TRY(launch_seed(dt, n, p, c->dist_bits, c->stream));
+    MPN_TRY(launch_propagate(c->variant, c->dist_bits, p, c->blocks, c->stream));
+    MPN_TRY(cudaEventRecord(c->ev[3], c->stream));
+    c->ev_prop = true;
+    c->stats_pending = true;
+    c->propagated = true;
+    c->last_max_layers = max_layers;
+    if (layers_run) {
+        st = finish_propagate(c);
+        if (st != MPN_OK) return st;
+        *layers_run = c->last_layers;
+    }
+    return MPN_OK;
+}
+
+mpn_status mpn_propagate_plain(mpn_ctx *c, const uint32_t *targets, int32_t n,
+                               uint32_t max_layers, int32_t check_every, uint32_t *layers_run) {
+    if (check_every < 1) return MPN_EINVAL;
+    const uint32_t *dt = nullptr;
+    mpn_status st = begin_propagate(c, targets, n, &dt);
+    if (st != MPN_OK) return st;
+    Ctl *ctl = (Ctl *)c->ctl.p;
+    const GridDev g = c->grid();
+    MPN_TRY(cudaEventRecord(c->ev[2], c->stream));
+    MPN_TRY(launch_plain_seed(dt, n, g, c->dist_bits, ctl, c->stream));
+    uint32_t layer = 1;
+    for (;;) {
+        for (int q = 0; q < check_every; ++q, ++layer) {
+            if (max_layers && layer > max_layers) break;
+            MPN_TRY(launch_plain_layer(g, c->dist_bits, layer, ctl, c->stream));
+        }
+        Ctl h;
+        MPN_TRY(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+        MPN_TRY(cudaStreamSynchronize(c->stream));
+        if (h.err) {
+            c->propagated = false;
+            return from_err_bits(h.err);
+        }
+        // stop once a layer added nothing, or the fixed depth is reached
+        if (h.plain_last + 1 < layer || (max_layers && layer > max_layers)) {
+            c->last_layers = h.plain_last;
+            break;
+        }
+    }
+    MPN_TRY(cudaEventRecord(c->ev[3], c->stream));
+    c->ev_prop = true;
+    c->propagated = true;
+    c->stats_pending = false;
+    c->last_max_layers = max_layers;
+    if (layers_run) *layers_run = c->last_layers;
+    return MPN_OK;
+}
+
+mpn_status mpn_sync(mpn_ctx *c) {
+    if (!c) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);
+    if (st != MPN_OK) return st;
+    return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+mpn_status mpn_get_distances(mpn_ctx *c, void *dst, int32_t on_device) {
+    if (!c || !dst) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);
+    if (st != MPN_OK) return st;
+    if (!c->propagated) return MPN_ESTATE;
+    MPN_TRY(cudaMemcpyAsync(dst, c->dist.p, c->dist_bytes(),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            c->stream));
+    return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+mpn_status mpn_get_activity(mpn_ctx *c, uint32_t L, int32_t *dst, int32_t on_device) {
+    if (!c || !dst) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);
+    if (st != MPN_OK) return st;
+    if (!c->propagated) return MPN_ESTATE;
+    if (L == 0) L = c->last_layers;
+    const size_t bytes = (size_t)c->H * c->W * sizeof(int32_t);
+    int32_t *out = dst;
+    if (!on_device) {
+        MPN_TRY(c->activity.ensure(bytes));
+        out = (int32_t *)c->activity.p;
+    }
+    MPN_TRY(launch_activity(c->grid(), c->dist_bits, L, out, c->stream));
+    if (!on_device)
+        MPN_TRY(cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, c->stream));
+    return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+static mpn_status trace_prepare(mpn_ctx *c, const uint32_t *starts, int32_t n,
+                                const uint32_t **ds, uint64_t *total) {
+    if (!c || n < 0 || (n > 0 && !starts)) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);
+    if (st != MPN_OK) return st;
+    if (!c->propagated) return MPN_ESTATE;
+    if (n > 0 && !is_device_ptr(starts)) {
+        const uint64_t N = (uint64_t)c->H * c->W;
+        for (int32_t i = 0; i < n; ++i)
+            if ((uint64_t)starts[i] >= N) return MPN_EINVAL;
+    }
+    st = stage_u32(c, c->starts, starts, n, ds);
+    if (st != MPN_OK) return st;
+    MPN_TRY(c->offsets.ensure((size_t)(n + 1) * sizeof(uint64_t)));
+    MPN_TRY(c->status.ensure((size_t)(n > 0 ? n : 1)));
+    Ctl *ctl = (Ctl *)c->ctl.p;
+    MPN_TRY(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), c->stream));
+    MPN_TRY(cudaMemsetAsync(c->offsets.p, 0, sizeof(uint64_t), c->stream));
+    if (n > 0) {
+        MPN_TRY(launch_trace_lengths(c->grid(), c->dist_bits, *ds, n, (uint64_t *)c->offsets.p,
+                                     (int8_t *)c->status.p, ctl, c->stream));
+        MPN_TRY(launch_scan((uint64_t *)c->offsets.p, n, c->stream));
+    }
+    uint32_t err = 0;
+    MPN_TRY(cudaMemcpyAsync(total, (uint64_t *)c->offsets.p + n, sizeof(uint64_t),
+                            cudaMemcpyDeviceToHost, c->stream));
+    MPN_TRY(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    MPN_TRY(cudaStreamSynchronize(c->stream));
+    if (err) return from_err_bits(err);
+    return MPN_OK;
+}
+
+mpn_status mpn_trace_lengths(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *offsets) {
+    if (!offsets) return MPN_EINVAL;
+    const uint32_t *ds = nullptr;
+    uint64_t total = 0;
+    mpn_status st = trace_prepare(c, starts, n, &ds, &total);
+    if (st != MPN_OK) return st;
+    MPN_TRY(cudaMemcpyAsync(offsets, c->offsets.p, (size_t)(n + 1) * sizeof(uint64_t),
+                            is_device_ptr(offsets) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            c->stream));
+    return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+mpn_status mpn_trace(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *offsets,
+                     uint32_t *cells, uint64_t cells_cap, int8_t *status) {
+    if (!offsets || (n > 0 && !status)) return MPN_EINVAL;
+    const uint32_t *ds = nullptr;
+    uint64_t total = 0;
+    mpn_status st = trace_prepare(c, starts, n, &ds, &total);
+    if (st != MPN_OK) return st;
+    const bool off_dev = is_device_ptr(offsets), st_dev = n > 0 && is_device_ptr(status);
+    MPN_TRY(cudaMemcpyAsync(offsets, c->offsets.p, (size_t)(n + 1) * sizeof(uint64_t),
+                            off_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (n > 0)
+        MPN_TRY(cudaMemcpyAsync(status, c->status.p, (size_t)n,
+                                st_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+    if (total > cells_cap) {
+        MPN_TRY(cudaStreamSynchronize(c->stream));
+        return MPN_ENOMEM;
+    }
+    if (total > 0 && !cells) return MPN_EINVAL;
+    const bool cells_dev = total > 0 && is_device_ptr(cells);
+    uint32_t *dcells = cells;
+    if (total > 0 && !cells_dev) {
+        MPN_TRY(c->cells.ensure((size_t)total * sizeof(uint32_t)));
+        dcells = (uint32_t *)c->cells.p;
+    }
+    Ctl *ctl = (Ctl *)c->ctl.p;
+    MPN_TRY(cudaEventRecord(c->ev[4], c->stream));
+    MPN_TRY(launch_trace(c->grid(), c->dist_bits, ds, n, (const uint64_t *)c->offsets.p,
+                         (const int8_t *)c->status.p, dcells, c->stream, &ctl->err));
+    MPN_TRY(cudaEventRecord(c->ev[5], c->stream));
+    c->ev_trace = true;
+    if (total > 0 && !cells_dev)
+        MPN_TRY(cudaMemcpyAsync(cells, dcells, (size_t)total * sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
+    uint32_t err = 0;
+    MPN_TRY(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    MPN_TRY(cudaStreamSynchronize(c->stream));
+    if (err) return (err & ERR_TRACE) ? MPN_ECUDA : from_err_bits(err);
+    return MPN_OK;
+}
+
+mpn_status mpn_get_stats(mpn_ctx *c, mpn_stats *out) {
+    if (!c || !out) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);
+    MPN_TRY(cudaStreamSynchronize(c->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->H = c->H;
+    out->W = c->W;
+    out->pitch_words = c->P;
+    out->dist_bits = c->dist_bits;
+    out->variant = c->variant;
+    out->depth = c->depth;
+    out->tiles_x = c->ntx;
+    out->tiles_y = c->nty;
+    out->blocks = c->blocks;
+    out->layers = c->last_layers;
+    out->sweeps = c->last_ctl.sweeps;
+    out->tile_visits = c->last_ctl.visits;
+    if (c->ev_enc) cudaEventElapsedTime(&c->ms_encode, c->ev[0], c->ev[1]);
+    if (c->ev_prop) cudaEventElapsedTime(&c->ms_propagate, c->ev[2], c->ev[3]);
+    if (c->ev_trace) cudaEventElapsedTime(&c->ms_trace, c->ev[4], c->ev[5]);
+    out->ms_encode = c->ms_encode;
+    out->ms_propagate = c->ms_propagate;
+    out->ms_trace = c->ms_trace;
+    return st;
+}
+
+void mpn_destroy(mpn_ctx *c) {
+    if (!c) return;
+    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    DevBuf *bufs[] = {&c->free_bits, &c->vis, &c->nb0, &c->nb1, &c->dist, &c->ctl, &c->tiles,
+                      &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
+                      &c->cells, &c->activity};
+    for (DevBuf *b : bufs) b->release();
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mpn.h"
+
+namespace mpn {
+
+// error bits the GPU records in Ctl::err
+constexpr uint32_t ERR_TIMEOUT = 1u;    // a grid-wide wait hit its iteration limit
+constexpr uint32_t ERR_OVERFLOW = 2u;   // a distance above 65534 in a uint16 plane
+constexpr uint32_t ERR_INVAL = 4u;      // a target index out of range
+constexpr uint32_t ERR_OBSTACLE = 8u;   // a target on an obstacle
+constexpr uint32_t ERR_SWEEPS = 16u;    // sweep count past the provable bound
+constexpr uint32_t ERR_TRACE = 32u;     // a walk found no neighbour one step closer
+
+// Border zones of a tile interior touched by frontier cells (frontier = cells
+// whose distance equals the last layer of a sweep). A zone bit says which
+// tile (itself or one of its 8 neighbours) the frontier can reach within the
+// next k layers, so that tile is queued for the next sweep.
+constexpr uint32_t FB_ANY = 1u, FB_N = 2u, FB_S = 4u, FB_W = 8u, FB_E = 16u;
+constexpr uint32_t FB_NW = 32u, FB_NE = 64u, FB_SW = 128u, FB_SE = 256u;
+
+// Device control block of one propagation (zeroed before each run).
+struct Ctl {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    unsigned int work[3];          // claim counters of the tile lists, by sweep mod 3
+    unsigned int list_len[3];      // lengths of the tile lists, by sweep mod 3
+    unsigned int err;
+    unsigned int max_layer;        // largest activation layer seen
+    unsigned int sweeps;
+    unsigned int plain_last;       // per-layer kernel: last layer that activated a cell
+    unsigned long long visits;     // tile visits
+};
+
+// Bit planes and distance plane of one grid. Bit b of word w in row y is cell
+// x = 32 * w + b; rows are P words apart (P a multiple of 4).
+struct GridDev {
+    const uint32_t *free_bits;   // 1 = free; bits at x >= W are 0
+    uint32_t *vis;               // 1 = reached
+    uint32_t *nb0, *nb1;         // cells first reached in the last sweep of that parity
+    void *dist;                  // H*W uint16 or uint32, row-major, pitch W
+    int H, W, P;
+};
+
+struct PropParams {
+    GridDev g;
+    uint32_t *queued;            // per tile: 1 + last sweep it was queued for
+    uint32_t *lists;             // 3 tile lists of ntx * nty entries, by sweep mod 3
+    Ctl *ctl;
+    int ntx, nty;                // tiles
+    int k;                       // temporal depth (layers per sweep), halo rows
+    int TY;                      // interior rows per tile
+    int TXW;                     // interior words per tile
+    uint32_t max_layers;         // 0 = until nothing changes
+    uint32_t spin_limit;         // barrier wait limit (iterations of ~100 ns)
+    uint32_t sweep_cap;          // more sweeps than this is an error
+};
+
+struct VariantDesc {
+    int rxw;      // region words (lanes per row group)
+    int r;        // rows per lane
+    int nwarps;   // warps per block
+};
+
+// ---- launch helpers implemented in the .cu files ----
+void count_launch(int n = 1);
+
+int num_variants();
+VariantDesc variant_desc(int v);
+cudaError_t propagate_blocks_per_sm(int v, int dist_bits, int *out);
+cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int blocks,
+                             cudaStream_t st);
+cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int dist_bits,
+                        cudaStream_t st);
+cudaError_t launch_plain_layer(const GridDev &g, int dist_bits, uint32_t layer, Ctl *ctl,
+                               cudaStream_t st);
+cudaError_t launch_plain_seed(const uint32_t *targets, int n, const GridDev &g, int dist_bits,
+                              Ctl *ctl, cudaStream_t st);
+
+cudaError_t launch_pack(const uint8_t *mask, int H, int W, int P, uint32_t *free_bits,
+                        cudaStream_t st);
+cudaError_t launch_repack(const uint32_t *src, int H, int W, int src_pitch, int P,
+                          uint32_t *free_bits, cudaStream_t st);
+
+cudaError_t launch_trace_lengths(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                                 uint64_t *lens_or_offsets, int8_t *status, Ctl *ctl,
+                                 cudaStream_t st);
+cudaError_t launch_scan(uint64_t *offsets, int n, cudaStream_t st);
+cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                         const uint64_t *offsets, const int8_t *status, uint32_t *cells,
+                         cudaStream_t st, uint32_t *err);
+cudaError_t launch_activity(const GridDev &g, int dist_bits, uint32_t L, int32_t *out,
+                            cudaStream_t st);
+
+}  // namespace mpn

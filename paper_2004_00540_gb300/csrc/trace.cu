@@ -1,0 +1,212 @@
+// Path reconstruction (Methods, "Path Reconstruction"): from a start, step to
+// the neighbour with the largest activity -- on the distance plane, a
+// neighbour with distance d - 1 -- until a target (d = 0). Ties go to the
+// lowest linear index, i.e. the first of (dy,dx) = (-1,-1), (-1,0), (-1,1),
+// (0,-1), (0,1), (1,-1), (1,0), (1,1).
+//
+// One warp per start. The walk is a chain of dependent steps, so its cost is
+// load latency, not bandwidth: the warp loads a 32 x 32 window of the distance
+// plane around the current cell with 32 coalesced row loads (one per lane per
+// row), then takes every step it can inside the window from shared memory
+// (eight lanes test the eight neighbours, a ballot picks the first), and only
+// reloads when the walk reaches the window's edge.
+#include <cuda_runtime.h>
+
+#include "mpn_internal.cuh"
+
+namespace mpn {
+
+namespace {
+
+constexpr int kWin = 32;          // window side (cells)
+constexpr int kWinPitch = 33;     // padded row pitch (bank spread)
+constexpr int kTraceWarps = 4;    // warps per block
+
+template <typename DT>
+__global__ void k_lengths(GridDev g, const uint32_t *__restrict__ starts, int n,
+                          uint64_t *__restrict__ offsets, int8_t *__restrict__ status,
+                          uint32_t *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) offsets[0] = 0ull;
+    if (i >= n) return;
+    const uint32_t s = starts[i];
+    uint64_t len = 0;
+    int8_t stt = MPN_PATH_OK;
+    if ((uint64_t)s >= (uint64_t)g.H * (uint64_t)g.W) {
+        atomicOr(err, ERR_INVAL);
+        stt = MPN_PATH_UNREACHABLE;
+    } else {
+        const int y = (int)(s / (uint32_t)g.W), x = (int)(s % (uint32_t)g.W);
+        const DT d = reinterpret_cast<const DT *>(g.dist)[s];
+        if (!((g.free_bits[(size_t)y * g.P + (x >> 5)] >> (x & 31)) & 1u)) stt = MPN_PATH_ON_OBSTACLE;
+        else if (d == (DT)~(DT)0) stt = MPN_PATH_UNREACHABLE;
+        else len = (uint64_t)d + 1u;
+    }
+    offsets[i + 1] = len;
+    status[i] = stt;
+}
+
+// In-place inclusive scan of a[1..n] by one block: chunks of blockDim * 8
+// elements, each thread summing 8 consecutive values, a warp-shuffle scan over
+// thread sums, and a running carry across chunks.
+__global__ void k_scan(uint64_t *a, int n) {
+    constexpr int ITEMS = 8;
+    __shared__ uint64_t warp_tot[32];
+    __shared__ uint64_t carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    if (tid == 0) carry_s = 0ull;
+    __syncthreads();
+    uint64_t *x = a + 1;
+    for (int base = 0; base < n; base += blockDim.x * ITEMS) {
+        uint64_t v[ITEMS];
+        uint64_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int idx = base + tid * ITEMS + j;
+            v[j] = (idx < n) ? x[idx] : 0ull;
+            sum += v[j];
+        }
+        uint64_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) warp_tot[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            uint64_t wt = (lane < nw) ? warp_tot[lane] : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t t = __shfl_up_sync(0xffffffffu, wt, o);
+                if (lane >= o) wt += t;
+            }
+            if (lane < nw) warp_tot[lane] = wt;
+        }
+        __syncthreads();
+        uint64_t run = carry_s + (wid > 0 ? warp_tot[wid - 1] : 0ull) + (inc - sum);
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int idx = base + tid * ITEMS + j;
+            run += v[j];
+            if (idx < n) x[idx] = run;
+        }
+        __syncthreads();
+        if (tid == 0) carry_s += warp_tot[nw - 1];
+        __syncthreads();
+    }
+}
+
+template <typename DT>
+__global__ void __launch_bounds__(kTraceWarps * 32)
+    k_trace(GridDev g, const uint32_t *__restrict__ starts, int n,
+            const uint64_t *__restrict__ offsets, const int8_t *__restrict__ status,
+            uint32_t *__restrict__ cells, uint32_t *err) {
+    __shared__ DT win[kTraceWarps][kWin * kWinPitch];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int i = blockIdx.x * kTraceWarps + wl;
+    if (i >= n) return;                         // whole warp leaves together
+    if (status[i] != MPN_PATH_OK) return;
+    const DT *dist = reinterpret_cast<const DT *>(g.dist);
+    const DT INF = (DT)~(DT)0;
+    DT *wb = win[wl];
+    // neighbour of lane q (q < 8) in the tie-break order
+    const int my_dy = (lane < 3) ? -1 : (lane < 5 ? 0 : 1);
+    const int my_dx = (lane == 0 || lane == 3 || lane == 5) ? -1 : ((lane == 1 || lane == 6) ? 0 : 1);
+
+    uint32_t c = starts[i];
+    uint64_t o = offsets[i];
+    int cy = (int)(c / (uint32_t)g.W), cx = (int)(c % (uint32_t)g.W);
+    uint32_t d = (uint32_t)dist[c];
+    if (lane == 0) cells[o] = c;
+    while (d > 0) {
+        const int wy0 = cy - kWin / 2, wx0 = cx - kWin / 2;
+        const int x = wx0 + lane;
+#pragma unroll 8
+        for (int r = 0; r < kWin; ++r) {
+            const int y = wy0 + r;
+            DT v = INF;
+            if (y >= 0 && y < g.H && x >= 0 && x < g.W) v = dist[(size_t)y * g.W + x];
+            wb[r * kWinPitch + lane] = v;
+        }
+        __syncwarp();
+        int ly = kWin / 2, lx = kWin / 2;
+        while (d > 0 && ly >= 1 && ly <= kWin - 2 && lx >= 1 && lx <= kWin - 2) {
+            bool hit = false;
+            if (lane < 8) hit = (uint32_t)wb[(ly + my_dy) * kWinPitch + lx + my_dx] == d - 1u;
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (!m) {                      // not a distance plane: give up on this path
+                if (lane == 0) atomicOr(err, ERR_TRACE);
+                return;
+            }
+            const int q = __ffs(m) - 1;
+            ly += __shfl_sync(0xffffffffu, my_dy, q);
+            lx += __shfl_sync(0xffffffffu, my_dx, q);
+            --d;
+            ++o;
+            if (lane == 0) cells[o] = (uint32_t)((wy0 + ly) * g.W + (wx0 + lx));
+        }
+        __syncwarp();
+        cy = wy0 + ly;
+        cx = wx0 + lx;
+    }
+}
+
+template <typename DT>
+__global__ void k_activity(GridDev g, uint32_t L, int32_t *out) {
+    const DT *dist = reinterpret_cast<const DT *>(g.dist);
+    const size_t n = (size_t)g.H * g.W;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const DT d = dist[i];
+        out[i] = (d != (DT)~(DT)0 && (uint32_t)d <= L) ? (int32_t)(L + 1u - (uint32_t)d) : 0;
+    }
+}
+
+int grid_for(size_t work_items, int per_block) {
+    size_t b = (work_items + per_block - 1) / per_block;
+    if (b > (size_t)152 * 32) b = (size_t)152 * 32;
+    return (int)(b ? b : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_trace_lengths(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                                 uint64_t *offsets, int8_t *status, Ctl *ctl, cudaStream_t st) {
+    const int tb = 256, nb = (n + 1 + tb - 1) / tb;
+    count_launch();
+    if (dist_bits == 16) k_lengths<uint16_t><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, &ctl->err);
+    else k_lengths<uint32_t><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, &ctl->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(uint64_t *offsets, int n, cudaStream_t st) {
+    count_launch();
+    k_scan<<<1, 1024, 0, st>>>(offsets, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                         const uint64_t *offsets, const int8_t *status, uint32_t *cells,
+                         cudaStream_t st, uint32_t *err) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = (n + kTraceWarps - 1) / kTraceWarps;
+    count_launch();
+    if (dist_bits == 16)
+        k_trace<uint16_t><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, offsets, status, cells, err);
+    else
+        k_trace<uint32_t><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, offsets, status, cells, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_activity(const GridDev &g, int dist_bits, uint32_t L, int32_t *out,
+                            cudaStream_t st) {
+    const size_t n = (size_t)g.H * g.W;
+    count_launch();
+    if (dist_bits == 16) k_activity<uint16_t><<<grid_for(n, 256), 256, 0, st>>>(g, L, out);
+    else k_activity<uint32_t><<<grid_for(n, 256), 256, 0, st>>>(g, L, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mpn

@@ -1,0 +1,318 @@
+"""Python binding of the C ABI in include/mpn.h (argument marshalling only).
+
+Every function has the C name and forwards to libmpn.so; all work runs in the
+library's CUDA kernels. Arrays may be numpy arrays (host memory) or torch
+tensors (host or CUDA); CUDA tensors are passed in place. There is no CPU
+fallback: if libmpn.so cannot be loaded the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpn.so")
+
+MPN_OK, MPN_EINVAL, MPN_ENOMEM, MPN_ECUDA, MPN_ETIMEOUT, MPN_EOVERFLOW, MPN_EOBSTACLE, MPN_ESTATE = range(8)
+MPN_DIST_AUTO, MPN_DIST_U16, MPN_DIST_U32 = 0, 16, 32
+MPN_UNREACHED16, MPN_UNREACHED32 = 0xFFFF, 0xFFFFFFFF
+MPN_PATH_OK, MPN_PATH_UNREACHABLE, MPN_PATH_ON_OBSTACLE = 0, 1, 2
+
+# every symbol include/mpn.h declares
+EXPORTS = (
+    "mpn_create", "mpn_create_packed", "mpn_set_mask", "mpn_set_stream", "mpn_propagate",
+    "mpn_propagate_plain", "mpn_get_distances", "mpn_get_activity", "mpn_trace_lengths",
+    "mpn_trace", "mpn_sync", "mpn_destroy", "mpn_status_str", "mpn_set_tuning",
+    "mpn_variant_info", "mpn_get_stats", "mpn_launch_count",
+)
+
+
+class MPNError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_name(status)} ({status})")
+        self.status = status
+
+
+class mpn_stats(ctypes.Structure):
+    _fields_ = [
+        ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("pitch_words", ctypes.c_int32),
+        ("dist_bits", ctypes.c_int32), ("variant", ctypes.c_int32), ("depth", ctypes.c_int32),
+        ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("blocks", ctypes.c_int32),
+        ("layers", ctypes.c_uint32), ("sweeps", ctypes.c_uint32), ("tile_visits", ctypes.c_uint64),
+        ("ms_encode", ctypes.c_float), ("ms_propagate", ctypes.c_float), ("ms_trace", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH, build_if_missing: bool = True):
+    """Load libmpn.so (building it with nvcc first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path) and build_if_missing:
+            from . import build as _b
+            _b.build()
+        if not os.path.exists(path):
+            raise ImportError(f"libmpn.so not found at {path}; run paper_2004_00540_gb300/build.py")
+        L = ctypes.CDLL(path)
+        vp, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "mpn_create": ([vp, i32, i32, i32, vp, pp], ctypes.c_int),
+            "mpn_create_packed": ([vp, i32, i32, i32, i32, vp, pp], ctypes.c_int),
+            "mpn_set_mask": ([vp, vp], ctypes.c_int),
+            "mpn_set_stream": ([vp, vp], ctypes.c_int),
+            "mpn_propagate": ([vp, vp, i32, u32, ctypes.POINTER(u32)], ctypes.c_int),
+            "mpn_propagate_plain": ([vp, vp, i32, u32, i32, ctypes.POINTER(u32)], ctypes.c_int),
+            "mpn_get_distances": ([vp, vp, i32], ctypes.c_int),
+            "mpn_get_activity": ([vp, u32, vp, i32], ctypes.c_int),
+            "mpn_trace_lengths": ([vp, vp, i32, vp], ctypes.c_int),
+            "mpn_trace": ([vp, vp, i32, vp, vp, u64, vp], ctypes.c_int),
+            "mpn_sync": ([vp], ctypes.c_int),
+            "mpn_destroy": ([vp], None),
+            "mpn_status_str": ([ctypes.c_int], ctypes.c_char_p),
+            "mpn_set_tuning": ([vp, i32, i32], ctypes.c_int),
+            "mpn_variant_info": ([i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)],
+                                 ctypes.c_int),
+            "mpn_get_stats": ([vp, ctypes.POINTER(mpn_stats)], ctypes.c_int),
+            "mpn_launch_count": ([], u64),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def status_name(s: int) -> str:
+    names = ["MPN_OK", "MPN_EINVAL", "MPN_ENOMEM", "MPN_ECUDA", "MPN_ETIMEOUT", "MPN_EOVERFLOW",
+             "MPN_EOBSTACLE", "MPN_ESTATE"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _check(st: int, what: str):
+    if st != MPN_OK:
+        raise MPNError(st, what)
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None, False
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, False
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), a.device.type == "cuda"
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- C-named functions -------------------------------------------------
+
+def mpn_create(mask, H: int, W: int, dist_bits: int = MPN_DIST_AUTO, stream=None):
+    L = load()
+    out = ctypes.c_void_p()
+    p, _ = _ptr(mask)
+    _check(L.mpn_create(p, H, W, dist_bits, _stream_handle(stream), ctypes.byref(out)), "mpn_create")
+    return out
+
+
+def mpn_create_packed(bits, H: int, W: int, pitch_words: int, dist_bits: int = MPN_DIST_AUTO,
+                      stream=None):
+    L = load()
+    out = ctypes.c_void_p()
+    p, _ = _ptr(bits)
+    _check(L.mpn_create_packed(p, H, W, pitch_words, dist_bits, _stream_handle(stream),
+                               ctypes.byref(out)), "mpn_create_packed")
+    return out
+
+
+def mpn_set_mask(ctx, mask):
+    _check(load().mpn_set_mask(ctx, _ptr(mask)[0]), "mpn_set_mask")
+
+
+def mpn_set_stream(ctx, stream):
+    _check(load().mpn_set_stream(ctx, _stream_handle(stream)), "mpn_set_stream")
+
+
+def mpn_propagate(ctx, targets, max_layers: int = 0, wait: bool = True):
+    """Returns the layer count (largest finite distance) when wait, else None."""
+    n = int(targets.numel() if hasattr(targets, "numel") else np.asarray(targets).size)
+    p, _ = _ptr(targets)
+    if wait:
+        lr = ctypes.c_uint32(0)
+        _check(load().mpn_propagate(ctx, p, n, max_layers, ctypes.byref(lr)), "mpn_propagate")
+        return int(lr.value)
+    _check(load().mpn_propagate(ctx, p, n, max_layers, None), "mpn_propagate")
+    return None
+
+
+def mpn_propagate_plain(ctx, targets, max_layers: int = 0, check_every: int = 1):
+    n = int(targets.numel() if hasattr(targets, "numel") else np.asarray(targets).size)
+    lr = ctypes.c_uint32(0)
+    _check(load().mpn_propagate_plain(ctx, _ptr(targets)[0], n, max_layers, check_every,
+                                      ctypes.byref(lr)), "mpn_propagate_plain")
+    return int(lr.value)
+
+
+def mpn_get_distances(ctx, out):
+    p, dev = _ptr(out)
+    _check(load().mpn_get_distances(ctx, p, int(dev)), "mpn_get_distances")
+    return out
+
+
+def mpn_get_activity(ctx, L: int, out):
+    p, dev = _ptr(out)
+    _check(load().mpn_get_activity(ctx, L, p, int(dev)), "mpn_get_activity")
+    return out
+
+
+def mpn_trace_lengths(ctx, starts, offsets):
+    n = int(starts.numel() if hasattr(starts, "numel") else np.asarray(starts).size)
+    _check(load().mpn_trace_lengths(ctx, _ptr(starts)[0], n, _ptr(offsets)[0]), "mpn_trace_lengths")
+    return offsets
+
+
+def mpn_trace(ctx, starts, offsets, cells, cells_cap: int, status):
+    """Returns the status code (MPN_OK or MPN_ENOMEM when cells is too small)."""
+    n = int(starts.numel() if hasattr(starts, "numel") else np.asarray(starts).size)
+    st = load().mpn_trace(ctx, _ptr(starts)[0], n, _ptr(offsets)[0], _ptr(cells)[0], cells_cap,
+                          _ptr(status)[0])
+    if st not in (MPN_OK, MPN_ENOMEM):
+        raise MPNError(st, "mpn_trace")
+    return st
+
+
+def mpn_sync(ctx):
+    _check(load().mpn_sync(ctx), "mpn_sync")
+
+
+def mpn_destroy(ctx):
+    if ctx:
+        load().mpn_destroy(ctx)
+
+
+def mpn_status_str(s: int) -> str:
+    return load().mpn_status_str(s).decode()
+
+
+def mpn_set_tuning(ctx, variant: int, depth: int):
+    _check(load().mpn_set_tuning(ctx, variant, depth), "mpn_set_tuning")
+
+
+def mpn_variant_info(v: int):
+    r, w, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    st = load().mpn_variant_info(v, ctypes.byref(r), ctypes.byref(w), ctypes.byref(t))
+    if st != MPN_OK:
+        return None
+    return {"region_rows": r.value, "region_words": w.value, "threads": t.value}
+
+
+def mpn_get_stats(ctx) -> dict:
+    s = mpn_stats()
+    _check(load().mpn_get_stats(ctx, ctypes.byref(s)), "mpn_get_stats")
+    return s.as_dict()
+
+
+def mpn_launch_count() -> int:
+    return int(load().mpn_launch_count())
+
+
+# ---- convenience wrapper -----------------------------------------------
+
+@dataclass
+class Paths:
+    offsets: np.ndarray   # uint64[n+1]
+    cells: np.ndarray     # uint32[offsets[-1]]
+    status: np.ndarray    # int8[n]
+
+    def path(self, i: int) -> np.ndarray:
+        return self.cells[int(self.offsets[i]):int(self.offsets[i + 1])]
+
+
+class Planner:
+    """One grid resident on the GPU: encode once, propagate and trace many times."""
+
+    def __init__(self, mask, dist_bits: int = MPN_DIST_AUTO, stream=None):
+        shape = tuple(mask.shape)
+        if len(shape) != 2:
+            raise ValueError("mask must be 2-D (H, W)")
+        self.H, self.W = int(shape[0]), int(shape[1])
+        self.ctx = mpn_create(mask, self.H, self.W, dist_bits, stream)
+        self.dist_bits = mpn_get_stats(self.ctx)["dist_bits"]
+        self.layers = None
+
+    def close(self):
+        if self.ctx:
+            mpn_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_tuning(self, variant: int, depth: int):
+        mpn_set_tuning(self.ctx, variant, depth)
+
+    def propagate(self, targets, max_layers: int = 0, plain: bool = False, check_every: int = 1):
+        t = np.ascontiguousarray(targets, np.uint32) if not hasattr(targets, "data_ptr") else targets
+        if plain:
+            self.layers = mpn_propagate_plain(self.ctx, t, max_layers, check_every)
+        else:
+            self.layers = mpn_propagate(self.ctx, t, max_layers)
+        return self.layers
+
+    def distances(self) -> np.ndarray:
+        out = np.empty((self.H, self.W), np.uint16 if self.dist_bits == 16 else np.uint32)
+        return mpn_get_distances(self.ctx, out)
+
+    def activity(self, L: int = 0) -> np.ndarray:
+        out = np.empty((self.H, self.W), np.int32)
+        return mpn_get_activity(self.ctx, L, out)
+
+    def trace(self, starts) -> Paths:
+        s = np.ascontiguousarray(starts, np.uint32)
+        n = s.size
+        offsets = np.zeros(n + 1, np.uint64)
+        mpn_trace_lengths(self.ctx, s, offsets)
+        total = int(offsets[-1])
+        cells = np.zeros(max(total, 1), np.uint32)
+        status = np.zeros(max(n, 1), np.int8)
+        st = mpn_trace(self.ctx, s, offsets, cells, total, status)
+        if st != MPN_OK:
+            raise MPNError(st, "mpn_trace")
+        return Paths(offsets, cells[:total], status[:n])
+
+    def stats(self) -> dict:
+        return mpn_get_stats(self.ctx)

@@ -1,0 +1,219 @@
+"""CUDA path vs the CPU oracle, bit for bit: distance planes, layer counts,
+path offsets, cells and per-start status, on seeded inputs that span many
+tiles with ragged edges, every compiled tile shape and several temporal
+depths, both distance dtypes, and the five named workloads."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2004_00540_gb300 as pkg
+from gpu_util import assert_parity, gpu_solve, widen
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_case(H, W, p, nt, ns, seed):
+    m = synth.bernoulli(H, W, p, seed) if p > 0 else synth.empty(H, W)
+    nfree = int((m == 0).sum())
+    if nfree == 0:
+        m.reshape(-1)[0] = 0
+        nfree = 1
+    t = synth.sample_free(m, min(nt, nfree), seed + 1)
+    s = np.random.default_rng(seed).integers(0, H * W, size=ns).astype(np.uint32)
+    return m, t, s
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (1, 77), (93, 1), (2, 2), (37, 1000), (300, 301),
+                                 (777, 513), (1000, 1000), (257, 4099)])
+@pytest.mark.parametrize("p", [0.0, 0.3])
+def test_random_grids_default_tiling(H, W, p):
+    m, t, s = rand_case(H, W, p, 3, 60, H * 7919 + W)
+    assert_parity(m, t, s)
+
+
+@pytest.mark.parametrize("variant", range(5))
+@pytest.mark.parametrize("depth", [1, 5, 16, 32])
+def test_every_variant_and_depth(variant, depth):
+    info = pkg.mpn_variant_info(variant)
+    if info["region_rows"] - 2 * depth < 1:
+        pytest.skip("depth too large for this region")
+    m, t, s = rand_case(611, 1403, 0.3, 4, 80, 17 + variant * 40 + depth)
+    assert_parity(m, t, s, variant=variant, depth=depth)
+
+
+@pytest.mark.parametrize("variant", range(5))
+def test_empty_grid_corner_source(variant):
+    # worst case for sweeps: one source in a corner of an empty grid
+    H, W = 900, 1300
+    m = synth.empty(H, W)
+    s = np.array([H * W - 1, (H - 1) * W, W - 1, 450 * W + 650], np.uint32)
+    stats = assert_parity(m, np.array([0], np.uint32), s, variant=variant, depth=32)
+    assert stats["layers"] == max(H, W) - 1
+
+
+@pytest.mark.parametrize("bits", [16, 32])
+def test_dtypes(bits):
+    m, t, s = rand_case(200, 250, 0.25, 2, 40, 5)
+    d, L, paths, stats = gpu_solve(m, t, s, dist_bits=bits)
+    assert d.dtype == (np.uint16 if bits == 16 else np.uint32)
+    assert stats["dist_bits"] == bits
+    assert_parity(m, t, s, dist_bits=bits)
+
+
+def test_u16_overflow_reported():
+    # a corridor longer than 65534 steps cannot fit a uint16 plane
+    m = synth.empty(1, 70000)
+    with pkg.Planner(m, pkg.MPN_DIST_U16) as pl:
+        with pytest.raises(pkg.MPNError) as e:
+            pl.propagate(np.array([0], np.uint32))
+        assert e.value.status == pkg.MPN_EOVERFLOW
+
+
+@pytest.mark.parametrize("L", [1, 2, 7, 40, 1000])
+def test_fixed_depth_network(L):
+    m, t, s = rand_case(400, 380, 0.3, 2, 50, 99)
+    assert_parity(m, t, s, max_layers=L)
+    assert_parity(m, t, s, max_layers=L, variant=2, depth=13)
+
+
+@pytest.mark.parametrize("check_every", [1, 16])
+def test_plain_per_layer_kernel(check_every):
+    m, t, s = rand_case(300, 333, 0.3, 3, 40, 3)
+    assert_parity(m, t, s, plain=True, check_every=check_every)
+    w = synth.c1_small()
+    assert_parity(w.mask, w.targets, w.starts, plain=True)
+    assert_parity(m, t, s, plain=True, max_layers=25)
+
+
+def test_activity_map_matches_literal_recurrence():
+    for seed in range(4):
+        m, t, _ = rand_case(40 + seed, 57, 0.3, 1 + seed, 1, 300 + seed)
+        with pkg.Planner(m) as pl:
+            layers = pl.propagate(t)
+            for L in (1, 3, layers, layers + 5):
+                got = pl.activity(L)
+                assert np.array_equal(got, oracle.omap(m, t, L)), L
+            assert np.array_equal(pl.activity(0), oracle.omap(m, t, layers))
+
+
+def test_errors_and_states():
+    m = synth.bernoulli(50, 60, 0.3, 1)
+    obst = int(np.flatnonzero(m.reshape(-1))[0])
+    free = int(np.flatnonzero(m.reshape(-1) == 0)[0])
+    with pkg.Planner(m) as pl:
+        with pytest.raises(pkg.MPNError) as e:
+            pl.trace(np.array([free], np.uint32))
+        assert e.value.status == pkg.MPN_ESTATE
+        with pytest.raises(pkg.MPNError) as e:
+            pl.propagate(np.array([obst], np.uint32))
+        assert e.value.status == pkg.MPN_EOBSTACLE
+        with pytest.raises(pkg.MPNError) as e:
+            pl.propagate(np.array([50 * 60], np.uint32))
+        assert e.value.status == pkg.MPN_EINVAL
+        with pytest.raises(pkg.MPNError) as e:
+            pl.propagate(np.array([], np.uint32))
+        assert e.value.status == pkg.MPN_EINVAL
+        pl.propagate(np.array([free], np.uint32))
+        with pytest.raises(pkg.MPNError) as e:
+            pl.trace(np.array([50 * 60 + 5], np.uint32))
+        assert e.value.status == pkg.MPN_EINVAL
+        # too small an output: offsets still filled, status ENOMEM
+        st = np.array([free, 50 * 60 - 1, obst], np.uint32)
+        off = np.zeros(4, np.uint64)
+        cells = np.zeros(1, np.uint32)
+        status = np.zeros(3, np.int8)
+        r = pkg.mpn_trace(pl.ctx, st, off, cells, 0, status)
+        d = pl.distances()
+        want_total = 1 + (0 if d.reshape(-1)[50 * 60 - 1] == 0xFFFF or m.reshape(-1)[-1]
+                          else int(d.reshape(-1)[50 * 60 - 1]) + 1)
+        assert r == pkg.MPN_ENOMEM and int(off[-1]) == want_total
+        assert status[2] == pkg.MPN_PATH_ON_OBSTACLE
+        # empty start list is fine
+        p = pl.trace(np.array([], np.uint32))
+        assert p.offsets.tolist() == [0]
+
+
+def test_device_tensors_in_and_out():
+    torch = pytest.importorskip("torch")
+    m, t, s = rand_case(513, 700, 0.3, 3, 30, 12)
+    dm = torch.from_numpy(m).cuda()
+    dt = torch.from_numpy(t.astype(np.int32)).cuda()
+    ds = torch.from_numpy(s.astype(np.int32)).cuda()
+    stream = torch.cuda.current_stream()
+    ctx = pkg.mpn_create(dm, 513, 700, 32, stream)
+    try:
+        L = pkg.mpn_propagate(ctx, dt)
+        dd = torch.empty((513, 700), dtype=torch.int32, device="cuda")
+        pkg.mpn_get_distances(ctx, dd)
+        off = torch.zeros(31, dtype=torch.int64, device="cuda")
+        pkg.mpn_trace_lengths(ctx, ds, off)
+        total = int(off[-1].item())
+        cells = torch.zeros(max(total, 1), dtype=torch.int32, device="cuda")
+        status = torch.zeros(30, dtype=torch.int8, device="cuda")
+        assert pkg.mpn_trace(ctx, ds, off, cells, total, status) == pkg.MPN_OK
+        torch.cuda.synchronize()
+    finally:
+        pkg.mpn_destroy(ctx)
+    od, oL = oracle.bfs(m, t)
+    assert L == oL
+    assert np.array_equal(dd.cpu().numpy().view(np.uint32), od)
+    ooff, ocells, ostatus = oracle.trace(m, od, s)
+    assert np.array_equal(off.cpu().numpy().view(np.uint64), ooff)
+    assert np.array_equal(cells.cpu().numpy().view(np.uint32)[:total], ocells)
+    assert np.array_equal(status.cpu().numpy(), ostatus)
+
+
+def test_packed_input_and_set_mask():
+    m, t, s = rand_case(130, 200, 0.3, 2, 20, 8)
+    P = 8
+    bits = np.zeros((130, P), np.uint32)
+    free = (m == 0)
+    for x in range(200):
+        bits[:, x // 32] |= (free[:, x].astype(np.uint32) << np.uint32(x % 32))
+    bits[:, 7] = 0xFFFFFFFF                      # junk past the row must be ignored
+    ctx = pkg.mpn_create_packed(bits, 130, 200, P, 32)
+    try:
+        L = pkg.mpn_propagate(ctx, t)
+        d = np.empty((130, 200), np.uint32)
+        pkg.mpn_get_distances(ctx, d)
+    finally:
+        pkg.mpn_destroy(ctx)
+    od, oL = oracle.bfs(m, t)
+    assert L == oL and np.array_equal(d, od)
+    m2, t2, s2 = rand_case(130, 200, 0.2, 2, 20, 9)
+    with pkg.Planner(m) as pl:
+        pl.propagate(t)
+        pkg.mpn_set_mask(pl.ctx, m2)
+        with pytest.raises(pkg.MPNError):
+            pl.distances()                        # new mask invalidates distances
+        pl.propagate(t2)
+        assert np.array_equal(widen(pl.distances()), oracle.bfs(m2, t2)[0])
+
+
+def test_workload_c1_small():
+    w = synth.c1_small()
+    assert_parity(w.mask, w.targets, w.starts, dist_bits=16)
+
+
+def test_workload_c2_maze():
+    w = synth.c2_maze()
+    stats = assert_parity(w.mask, w.targets, w.starts)
+    assert stats["layers"] > 1000
+
+
+def test_workload_c3_maze_open():
+    w = synth.c3_maze_open()
+    assert_parity(w.mask, w.targets, w.starts)
+
+
+@pytest.mark.parametrize("i", [0, 1, 2, 3, 10, 11, 100, 101, 254, 255])
+def test_workload_c4_members(i):
+    w = synth.c4_member(i)
+    assert_parity(w.mask, w.targets, w.starts, dist_bits=w.dist_bits)
+
+
+def test_workload_c5_huge_full():
+    w = synth.c5_huge()
+    stats = assert_parity(w.mask, w.targets, w.starts)
+    assert stats["layers"] > 100

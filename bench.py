@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the max-pooling path planner on one GB300 (or N, one process
+per GPU, each solving its own copy of the workload).
+
+A step is one pass of the whole hot path over the 23170 x 23170 grid
+(Bernoulli(0.25) obstacles plus rectangles covering 10 %, 64 targets, 4000
+starts): encode the uint8 mask to bits, propagate the activity wave to
+convergence, trace all 4000 paths. Inputs are resident in HBM when the timed
+region starts (value); e2e repeats the step through the C ABI from pinned host
+buffers, with the mask upload and the distance-map and path downloads inside
+the timed region.
+
+metric: effective cell-updates/s = H * W * L / t, L = the number of layers the
+paper's network needs (the largest finite distance), as in the paper's O(N L)
+complexity (Methods, "Determining the number of layers L").
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs the same step on its own GPU; rank 0 prints one
+JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "effective cell-updates/sec"
+UNIT = "cell-updates/s"
+BYTES_PER_UPDATE_U32 = 8.125      # read the mask bit, read and write the uint32 distance
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--side", type=int, default=23170, help="grid side (default: the full workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--depth", type=int, default=32)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.idx = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def shard(n_items: int, rank: int, world: int):
+    """Indices of the independent problems rank `rank` of `world` solves
+    (round robin; the ranks never exchange data)."""
+    return list(range(rank, n_items, world))
+
+
+def aggregate(local_ms: float, units_per_rank: float, steps: int, world: int, dist=None, device=None):
+    """Whole-job time = the slowest rank's time (all-reduce MAX); value =
+    the units all ranks processed / that time."""
+    t = local_ms
+    if dist is not None and world > 1:
+        import torch
+        tt = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, world * units_per_rank * steps / (t * 1e-3)
+
+
+def workload(side: int):
+    if side == 23170:
+        return synth.c5_huge()
+    return synth.c5_huge(side=side)
+
+
+def crop(w, side):
+    """Top-left side x side window of a workload (end-points that fall inside)."""
+    m = np.ascontiguousarray(w.mask[:side, :side])
+    def keep(idx):
+        y, x = idx // w.W, idx % w.W
+        ok = (y < side) & (x < side)
+        return (y[ok] * side + x[ok]).astype(np.uint32)
+    t = keep(w.targets.astype(np.int64))
+    s = keep(w.starts.astype(np.int64))
+    return synth.Workload(f"{w.name}_crop{side}", m, t, s, 32, dict(w.meta))
+
+
+def time_oracle(w, reps=1):
+    """The CPU oracle as it stands: BFS + trace, single thread."""
+    import oracle
+    best = None
+    L = 0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        d, L = oracle.bfs(w.mask, w.targets)
+        oracle.trace(w.mask, d, w.starts)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return best, L
+
+
+def cpu_baseline(w, sample_side=23170):
+    s = crop(w, sample_side) if sample_side < w.H else w
+    dt, L = time_oracle(s)
+    return {"value": s.H * s.W * L / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"top-left {s.H}x{s.W} window of the workload with the {s.targets.size} targets "
+                      f"and {s.starts.size} starts inside it (L={L}); single-thread BFS + trace, "
+                      f"{dt:.1f} s", "seconds": dt, "host_cores": os.cpu_count()}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = workload(args.side)
+    s = crop(w, min(8192, w.H))
+    times, L = [], 0
+    for i in range(args.warmup + args.steps):
+        dt, L = time_oracle(s)
+        if i >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    v = s.H * s.W * L * len(times) / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "sample": f"top-left {s.H}x{s.W} window", "layers": L},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"top-left {s.H}x{s.W} window of {w.name}, "
+                                       f"{s.targets.size} targets, {s.starts.size} starts"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2004_00540_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    w = workload(args.side)
+    H, W = w.H, w.W
+    stream = torch.cuda.Stream()
+    d_mask = torch.from_numpy(w.mask).cuda()
+    d_t = torch.from_numpy(w.targets.view(np.int32)).cuda()
+    d_s = torch.from_numpy(w.starts.view(np.int32)).cuda()
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        ctx = pkg.mpn_create(d_mask, H, W, pkg.MPN_DIST_U32, stream)
+    if args.variant >= 0:
+        pkg.mpn_set_tuning(ctx, args.variant, args.depth)
+    # device-resident outputs, sized once
+    L = pkg.mpn_propagate(ctx, d_t)
+    n = w.starts.size
+    d_off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    pkg.mpn_trace_lengths(ctx, d_s, d_off)
+    total = int(d_off[-1].item())
+    d_cells = torch.zeros(max(total, 1), dtype=torch.int32, device="cuda")
+    d_status = torch.zeros(n, dtype=torch.int8, device="cuda")
+
+    def step():
+        pkg.mpn_set_mask(ctx, d_mask)
+        pkg.mpn_propagate(ctx, d_t, 0, wait=False)
+        st = pkg.mpn_trace(ctx, d_s, d_off, d_cells, total, d_status)
+        assert st == pkg.MPN_OK
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    stats0 = pkg.mpn_get_stats(ctx)
+
+    # timed region: K steps bracketed by barrier + synchronize; events on the
+    # library's stream; per-kernel propagate time from the library's events
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "") or "")
+    clocks = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else (uuid or str(local)))
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = pkg.mpn_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    prop_ms = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        prop_ms.append(pkg.mpn_get_stats(ctx)["ms_propagate"])
+    ev1.record(stream)
+    ev1.synchronize()
+    launches = pkg.mpn_launch_count() - launches0
+    t_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    st = pkg.mpn_get_stats(ctx)
+    L = st["layers"]
+    units = float(H) * W * L
+    t_ms, value = aggregate(t_ms, units, args.steps, world, pg, "cuda")
+    if pg:
+        pg.barrier()
+    prop_avg = sum(prop_ms) / len(prop_ms)
+
+    # roofline of the dominant kernel (the persistent propagation kernel)
+    peak, peak_kind = peaks()
+    achieved = units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+            "kernel": "k_propagate", "ms_per_launch": prop_avg,
+            "note": "algorithmic bytes = 8.125 B per effective cell-update (mask bit + uint32 "
+                    "read + write per layer); temporal blocking does each update in registers"}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_mask = torch.from_numpy(w.mask).pin_memory()
+        h_t = torch.from_numpy(w.targets.view(np.int32)).pin_memory()
+        h_s = torch.from_numpy(w.starts.view(np.int32)).pin_memory()
+        h_dist = torch.empty((H, W), dtype=torch.int32).pin_memory()
+        h_off = torch.zeros(n + 1, dtype=torch.int64).pin_memory()
+        h_cells = torch.zeros(max(total, 1), dtype=torch.int32).pin_memory()
+        h_status = torch.zeros(n, dtype=torch.int8).pin_memory()
+
+        def e2e_step():
+            pkg.mpn_set_mask(ctx, h_mask)
+            pkg.mpn_propagate(ctx, h_t, 0, wait=False)
+            pkg.mpn_trace(ctx, h_s, h_off, h_cells, total, h_status)
+            pkg.mpn_get_distances(ctx, h_dist)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        ke = max(1, min(args.steps, 5))
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / ke
+        te_ms, e2e_value = aggregate(te * 1e3, units, 1, world, pg, "cuda")
+        e2e = {"value": e2e_value, "unit": UNIT, "ms_per_step": te_ms,
+               "h2d_bytes_per_step": int(H * W + 4 * w.targets.size + 4 * n),
+               "d2h_bytes_per_step": int(4 * H * W + 8 * (n + 1) + 4 * total + n + 8)}
+        assert int(h_off[-1]) == total
+
+    pkg.mpn_destroy(ctx)
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": w.name, "H": H, "W": W, "targets": int(w.targets.size),
+                   "starts": int(n), "layers": int(L), "path_cells": total,
+                   "step": "encode + propagate + trace", "parallelism": f"replicas x{world}",
+                   "variant": st["variant"], "depth": st["depth"],
+                   "l2": "inputs larger than L2 (uint8 mask 537 MB + uint32 distance plane 2.15 GB per step)"},
+        "propagate": {"ms": prop_avg, "effective_cell_updates_per_s": units / (prop_avg * 1e-3),
+                      "pct_hbm_roofline": 100 * units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / (peak * 1e9),
+                      "sweeps": st["sweeps"], "tile_visits": st["tile_visits"],
+                      "tiles": st["tiles_x"] * st["tiles_y"], "blocks": st["blocks"]},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if pg:
+        pg.destroy_process_group()
+    if not args.no_cpu and world == 1:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -119,7 +119,9 @@ mpn_status configure(mpn_ctx *c, int variant, int depth) {
     if (variant < 0 || variant >= num_variants()) return MPN_EINVAL;
     const VariantDesc vd = variant_desc(variant);
     const int ry = vd.nwarps * (32 / vd.rxw) * vd.r;
-    if (depth < 1 || depth > 32 || ry - 2 * depth < 1) return MPN_EINVAL;
+    // the halo (depth rows) must not reach past the neighbouring tiles: a
+    // visit queues only its 8 neighbours, so the interior needs >= depth rows
+    if (depth < 1 || depth > 32 || ry - 2 * depth < depth) return MPN_EINVAL;
     const int TY = ry - 2 * depth, TXW = vd.rxw - 2;
     const int wwords = (c->W + 31) / 32;
     const int ntx = (wwords + TXW - 1) / TXW, nty = (c->H + TY - 1) / TY;
@@ -369,8 +371,8 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     p.spin_limit = kSpinLimit;
     const uint64_t bound = (max_layers ? (uint64_t)max_layers : (uint64_t)c->H * c->W) / c->depth + 3;
     p.sweep_cap = (uint32_t)(bound < (1u << 22) ? bound : (1u << 22));
-    MPN_TRY(cudaEventRecord(c->ev[2], c->stream));
     MPN_TRY(launch_seed(dt, n, p, c->dist_bits, c->stream));
+    MPN_TRY(cudaEventRecord(c->ev[2], c->stream));   // times the persistent kernel alone
     MPN_TRY(launch_propagate(c->variant, c->dist_bits, p, c->blocks, c->stream));
     MPN_TRY(cudaEventRecord(c->ev[3], c->stream));
     c->ev_prop = true;

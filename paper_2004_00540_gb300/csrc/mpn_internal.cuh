@@ -64,6 +64,7 @@ struct VariantDesc {
     int rxw;      // region words (lanes per row group)
     int r;        // rows per lane
     int nwarps;   // warps per block
+    int minb;     // blocks per SM the register budget aims at
 };
 
 // ---- launch helpers implemented in the .cu files ----

@@ -88,13 +88,15 @@ __device__ bool grid_barrier(Ctl *c, unsigned nblocks, unsigned spin_limit) {
 
 // 3x3 dilation along the row: v | v shifted one cell left | one cell right,
 // with the carries from the neighbouring words of the same row (the lanes of
-// one row group hold consecutive words; the region edges see zeros).
+// one row group hold consecutive words). At the region's outer words the
+// shuffle returns the lane's own word, so the outermost cell of the region can
+// pick up a wrong bit; that error moves one cell per layer and, with a one-word
+// (32-cell) horizontal halo and at most 32 layers per visit, never reaches the
+// interior.
 template <int RXW>
-__device__ __forceinline__ uint32_t hdil(uint32_t v, int w) {
-    uint32_t left = __shfl_up_sync(0xffffffffu, v, 1, RXW);
-    uint32_t right = __shfl_down_sync(0xffffffffu, v, 1, RXW);
-    if (w == 0) left = 0u;
-    if (w == RXW - 1) right = 0u;
+__device__ __forceinline__ uint32_t hdil(uint32_t v) {
+    const uint32_t left = __shfl_up_sync(0xffffffffu, v, 1, RXW);
+    const uint32_t right = __shfl_down_sync(0xffffffffu, v, 1, RXW);
     return v | __funnelshift_l(left, v, 1) | __funnelshift_r(v, right, 1);
 }
 
@@ -146,25 +148,12 @@ __device__ void push_reached(const PropParams &p, int ty, int tx, uint32_t zones
     if (zones & FB_SE) push_tile(p, ty + 1, tx + 1, s);
 }
 
-template <typename DT>
-__device__ __forceinline__ void record(DT *row, uint32_t nv, uint32_t layer, Ctl *ctl) {
-    if (sizeof(DT) == 2 && layer > 0xfffeu) {
-        atomicOr(&ctl->err, ERR_OVERFLOW);
-        return;
-    }
-    while (nv) {
-        const int b = __ffs(nv) - 1;
-        nv &= nv - 1u;
-        row[b] = (DT)layer;
-    }
-}
-
 // Persistent temporally blocked propagation. Block = NW warps; a row group is
 // RXW consecutive lanes holding RXW consecutive words of R consecutive rows
 // (one word per lane per row, in registers). Region = (NW * 32 / RXW * R) rows
 // x RXW words; interior = rows [k, RY - k) x words [1, RXW - 1).
-template <int RXW, int R, int NW, typename DT>
-__global__ void __launch_bounds__(NW * 32) k_propagate(PropParams p) {
+template <int RXW, int R, int NW, int MINB, typename DT>
+__global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     static_assert(RXW == 4 || RXW == 8 || RXW == 16 || RXW == 32, "row group width");
     static_assert(R >= 2, "rows per lane");
     constexpr int GPW = 32 / RXW;
@@ -173,7 +162,7 @@ __global__ void __launch_bounds__(NW * 32) k_propagate(PropParams p) {
     __shared__ uint32_t xtop[2][G][RXW];
     __shared__ uint32_t xbot[2][G][RXW];
     __shared__ int s_tile;
-    __shared__ unsigned s_mask, s_lastj, s_done;
+    __shared__ unsigned s_mask[2], s_done, s_maxl;   // s_mask by visit parity
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = lane % RXW;
@@ -185,6 +174,9 @@ __global__ void __launch_bounds__(NW * 32) k_propagate(PropParams p) {
     DT *dist = reinterpret_cast<DT *>(gd.dist);
     const bool ownW = (w >= 1) && (w <= TXW);
     Ctl *ctl = p.ctl;
+    unsigned thr_maxl = 0u;              // largest layer this thread's words reached
+    unsigned long long blk_visits = 0;   // thread 0: tile visits of this block
+    unsigned vq = 0u;                    // visit parity (block-uniform)
 
     // the seeding step rejected the targets (nothing in this kernel sets these
     // bits, so every block takes the same branch)
@@ -202,82 +194,137 @@ __global__ void __launch_bounds__(NW * 32) k_propagate(PropParams p) {
         if (p.max_layers && l0 + (uint32_t)k > p.max_layers) jmax = (int)(p.max_layers - l0);
         uint32_t *nbS = (s & 1) ? gd.nb1 : gd.nb0;
         const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
+        unsigned *work = &ctl->work[s % 3];
         const uint32_t len = ld_acquire(&ctl->list_len[s % 3]);
 
-        for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t i = atomicAdd(work, 1u);
+            s_tile = (i < len) ? (int)ld_relaxed(list + i) : -1;
+        }
+        __syncthreads();
+        int t = s_tile;
+        while (t >= 0) {
+            // claim the next tile now; the atomic's latency hides behind this visit
+            uint32_t next_i = 0;
+            vq ^= 1u;
             if (threadIdx.x == 0) {
-                const uint32_t i = atomicAdd(&ctl->work[s % 3], 1u);
-                s_tile = (i < len) ? (int)ld_relaxed(list + i) : -1;
-                s_mask = 0u;
-                s_lastj = 0u;
+                next_i = atomicAdd(work, 1u);
+                s_mask[vq] = 0u;   // last read two visits ago, before the previous visit's first barrier
             }
-            __syncthreads();
-            const int t = s_tile;
-            __syncthreads();
-            if (t < 0) break;
 
             // ---- load the region (tile + halo) ----
             const int ty = t / p.ntx, tx = t - ty * p.ntx;
             const int y0 = ty * TY - k;
             const int gw = tx * TXW - 1 + w;
             const bool inX = (gw >= 0) && (gw < gd.P);
-            uint32_t V[R], F[R], NB[R];
+            uint32_t V[R], F[R], NB[R], OWN[R];   // OWN: all-ones on this tile's interior words
 #pragma unroll
             for (int i = 0; i < R; ++i) {
-                const int y = y0 + r0 + i;
+                const int rr = r0 + i, y = y0 + rr;
                 const bool in = inX && y >= 0 && y < gd.H;
+                const bool own = ownW && rr >= k && rr < k + TY;
                 const size_t off = (size_t)y * gd.P + gw;
+                OWN[i] = own ? 0xffffffffu : 0u;
                 F[i] = in ? __ldg(gd.free_bits + off) : 0u;
                 V[i] = in ? ld_relaxed(gd.vis + off) : 0u;
                 NB[i] = 0u;
             }
             __threadfence();   // visit bits before the matching this-sweep bits
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int rr = r0 + i, y = y0 + rr;
-                const bool own = ownW && rr >= k && rr < k + TY;
-                if (!own && V[i]) V[i] &= ~ld_relaxed(nbS + (size_t)y * gd.P + gw);
-            }
+            for (int i = 0; i < R; ++i)
+                if (!OWN[i] && V[i]) V[i] &= ~ld_relaxed(nbS + (size_t)(y0 + r0 + i) * gd.P + gw);
 
-            // ---- k layers in registers ----
-            uint32_t changed = 1u, fmask = 0u;
+            // ---- up to k layers in registers ----
+            // P[b][i]: bit b of (layer - l0 - 1) for cells first reached in
+            // this visit, so each cell's distance is written once, at the end.
+            uint32_t P[5][R];
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+#pragma unroll
+                for (int b = 0; b < 5; ++b) P[b][i] = 0u;
+            }
+            uint32_t changed = 1u;
             unsigned lastj = 0u;
             for (int j = 1; j <= jmax; ++j) {
-                const uint32_t hF = hdil<RXW>(V[0], w);
-                const uint32_t hL = hdil<RXW>(V[R - 1], w);
+                const uint32_t hF = hdil<RXW>(V[0]);
+                const uint32_t hL = hdil<RXW>(V[R - 1]);
                 xtop[j & 1][g][w] = hF;
                 xbot[j & 1][g][w] = hL;
                 if (!__syncthreads_or(changed != 0u)) break;   // region is stable
                 const uint32_t hUp = (g > 0) ? xbot[j & 1][g - 1][w] : 0u;
                 const uint32_t hDn = (g < G - 1) ? xtop[j & 1][g + 1][w] : 0u;
-                const uint32_t layer = l0 + (uint32_t)j;
+                uint32_t h[R];
+                h[0] = hF;
+                h[R - 1] = hL;
+#pragma unroll
+                for (int i = 1; i < R - 1; ++i) h[i] = hdil<RXW>(V[i]);
+                uint32_t M[5];   // all-ones where bit b of j - 1 is set (block-uniform)
+#pragma unroll
+                for (int b = 0; b < 5; ++b) M[b] = (((j - 1) >> b) & 1) ? 0xffffffffu : 0u;
                 changed = 0u;
-                uint32_t hPrev = hUp, hCur = hF;
+                uint32_t own_new = 0u;
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    uint32_t hNext;
-                    if (i + 1 < R - 1) hNext = hdil<RXW>(V[i + 1], w);
-                    else if (i + 1 == R - 1) hNext = hL;
-                    else hNext = hDn;
-                    const uint32_t nv = (hPrev | hCur | hNext) & F[i] & ~V[i];
-                    hPrev = hCur;
-                    hCur = hNext;
+                    const uint32_t up = (i > 0) ? h[i - 1] : hUp;
+                    const uint32_t dn = (i < R - 1) ? h[i + 1] : hDn;
+                    const uint32_t nv = (up | h[i] | dn) & F[i] & ~V[i];
                     V[i] |= nv;
                     changed |= nv;
-                    const int rr = r0 + i;
-                    if (nv && ownW && rr >= k && rr < k + TY) {
-                        NB[i] |= nv;
-                        lastj = (unsigned)j;
-                        record<DT>(dist + (size_t)(y0 + rr) * gd.W + (size_t)gw * 32, nv, layer,
-                                   ctl);
-                        if (j == k) fmask |= border_bits(rr - k, w - 1, nv, k, TY, TXW);
+                    const uint32_t onv = nv & OWN[i];
+                    NB[i] |= onv;
+                    own_new |= onv;
+#pragma unroll
+                    for (int b = 0; b < 5; ++b) P[b][i] |= onv & M[b];
+                }
+                if (own_new) lastj = (unsigned)j;
+            }
+
+            // the claimed index has arrived by now; fetch its tile id early
+            int next_t = -1;
+            if (threadIdx.x == 0 && next_i < len) next_t = (int)ld_relaxed(list + next_i);
+
+            // ---- frontier zones: cells reached at layer l0 + k ----
+            uint32_t fmask = 0u;
+            if (jmax == k) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    uint32_t last = NB[i];
+#pragma unroll
+                    for (int b = 0; b < 5; ++b)
+                        last &= (((k - 1) >> b) & 1) ? P[b][i] : ~P[b][i];
+                    fmask |= border_bits(r0 + i - k, w - 1, last, k, TY, TXW);
+                }
+            }
+            if (fmask) atomicOr(&s_mask[vq], fmask);
+            if (lastj) thr_maxl = max(thr_maxl, l0 + lastj);
+
+            // ---- distances of the cells first reached in this visit ----
+            // The warp writes one changed word at a time: 32 lanes, 32
+            // consecutive cells, one coalesced store.
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                unsigned act = __ballot_sync(0xffffffffu, NB[i] != 0u);
+                while (act) {
+                    const int src = __ffs(act) - 1;
+                    act &= act - 1u;
+                    const uint32_t nb = __shfl_sync(0xffffffffu, NB[i], src);
+                    uint32_t off = 0u;
+#pragma unroll
+                    for (int b = 0; b < 5; ++b)
+                        off |= ((__shfl_sync(0xffffffffu, P[b][i], src) >> lane) & 1u) << b;
+                    const int sw = src % RXW;                         // source word column
+                    const int sg = warp * GPW + src / RXW;            // source row group
+                    const int y = y0 + sg * R + i;
+                    const int gws = tx * TXW - 1 + sw;
+                    if ((nb >> lane) & 1u) {
+                        const uint32_t layer = l0 + 1u + off;
+                        if (sizeof(DT) == 2 && layer > 0xfffeu) atomicOr(&ctl->err, ERR_OVERFLOW);
+                        else dist[(size_t)y * gd.W + (size_t)gws * 32 + lane] = (DT)layer;
                     }
                 }
             }
 
-            // ---- publish: this-sweep bits, then visit bits, then summaries ----
-            if (fmask) atomicOr(&s_mask, fmask);
-            if (lastj) atomicMax(&s_lastj, lastj);
+            // ---- publish: this-sweep bits, then visit bits, then the queue ----
 #pragma unroll
             for (int i = 0; i < R; ++i)
                 if (NB[i]) st_relaxed(nbS + (size_t)(y0 + r0 + i) * gd.P + gw, NB[i]);
@@ -285,12 +332,17 @@ __global__ void __launch_bounds__(NW * 32) k_propagate(PropParams p) {
 #pragma unroll
             for (int i = 0; i < R; ++i)
                 if (NB[i]) st_relaxed(gd.vis + (size_t)(y0 + r0 + i) * gd.P + gw, V[i]);
-            __syncthreads();
             if (threadIdx.x == 0) {
-                if (s_mask) push_reached(p, ty, tx, s_mask, s + 1);
-                if (s_lastj) atomicMax(&ctl->max_layer, l0 + s_lastj);
-                atomicAdd(&ctl->visits, 1ull);
+                ++blk_visits;
+                s_tile = next_t;
             }
+            __syncthreads();
+            if (threadIdx.x < 9) {
+                // lanes 0..8 each queue one of the tiles the frontier reaches
+                const uint32_t zone = 1u << threadIdx.x;
+                if (s_mask[vq] & zone) push_reached(p, ty, tx, zone, s + 1);
+            }
+            t = s_tile;
         }
 
         if (!grid_barrier(ctl, gridDim.x, p.spin_limit)) return;
@@ -304,10 +356,17 @@ __global__ void __launch_bounds__(NW * 32) k_propagate(PropParams p) {
                 done = 1;
             }
             if (done && blockIdx.x == 0) ctl->sweeps = s + 1;
+            if (done && blk_visits) atomicAdd(&ctl->visits, blk_visits);
             s_done = done;
+            s_maxl = 0u;
         }
         __syncthreads();
-        if (s_done) return;
+        if (s_done) {
+            if (thr_maxl) atomicMax(&s_maxl, thr_maxl);
+            __syncthreads();
+            if (threadIdx.x == 0 && s_maxl) atomicMax(&ctl->max_layer, s_maxl);
+            return;
+        }
     }
 }
 
@@ -377,32 +436,34 @@ __global__ void k_plain_layer(GridDev g, uint32_t layer, Ctl *ctl) {
     if (who && (threadIdx.x & 31) == __ffs(who) - 1) atomicMax(&ctl->plain_last, layer);
 }
 
-template <int RXW, int R, int NW>
-struct Variant {
-    template <typename DT>
-    static void *fn() {
-        return (void *)k_propagate<RXW, R, NW, DT>;
-    }
-};
+template <int RXW, int R, int NW, int MINB>
+void *variant_ptr(bool u16) {
+    return u16 ? (void *)k_propagate<RXW, R, NW, MINB, uint16_t>
+               : (void *)k_propagate<RXW, R, NW, MINB, uint32_t>;
+}
 
-// Compiled tile shapes: {region words, rows per lane, warps per block}.
-// Region rows = warps * (32 / words) * rows per lane.
+// Compiled tile shapes: {region words, rows per lane, warps per block, blocks
+// per SM the register budget aims at}. Region rows = warps * (32 / words) *
+// rows per lane; interior = region minus k rows top and bottom and one word
+// left and right.
 constexpr VariantDesc kVariants[] = {
-    {8, 8, 8},     // 256 rows x 256 cells (interior 192 cells wide)
-    {16, 16, 8},   // 256 rows x 512 cells
-    {8, 4, 8},     // 128 rows x 256 cells
-    {16, 32, 8},   // 512 rows x 512 cells
-    {32, 16, 8},   // 128 rows x 1024 cells
+    {8, 4, 8, 3},    // 128 rows x 256 cells
+    {8, 8, 8, 2},    // 256 rows x 256 cells
+    {16, 4, 8, 3},   //  64 rows x 512 cells
+    {4, 8, 8, 2},    // 512 rows x 128 cells
+    {8, 4, 4, 5},    //  64 rows x 256 cells
+    {16, 8, 8, 2},   // 128 rows x 512 cells
 };
 
 void *variant_fn(int v, int dist_bits) {
     const bool u16 = dist_bits == 16;
     switch (v) {
-        case 0: return u16 ? Variant<8, 8, 8>::fn<uint16_t>() : Variant<8, 8, 8>::fn<uint32_t>();
-        case 1: return u16 ? Variant<16, 16, 8>::fn<uint16_t>() : Variant<16, 16, 8>::fn<uint32_t>();
-        case 2: return u16 ? Variant<8, 4, 8>::fn<uint16_t>() : Variant<8, 4, 8>::fn<uint32_t>();
-        case 3: return u16 ? Variant<16, 32, 8>::fn<uint16_t>() : Variant<16, 32, 8>::fn<uint32_t>();
-        case 4: return u16 ? Variant<32, 16, 8>::fn<uint16_t>() : Variant<32, 16, 8>::fn<uint32_t>();
+        case 0: return variant_ptr<8, 4, 8, 3>(u16);
+        case 1: return variant_ptr<8, 8, 8, 2>(u16);
+        case 2: return variant_ptr<16, 4, 8, 3>(u16);
+        case 3: return variant_ptr<4, 8, 8, 2>(u16);
+        case 4: return variant_ptr<8, 4, 4, 5>(u16);
+        case 5: return variant_ptr<16, 8, 8, 2>(u16);
         default: return nullptr;
     }
 }

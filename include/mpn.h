@@ -168,8 +168,9 @@ const char *mpn_status_str(mpn_status s);
 /*
  * Propagation tiling. variant: index into the compiled tile shapes
  * (mpn_variant_info); depth: temporal blocking depth k = layers advanced per
- * tile visit, 1..32 (also the halo width in rows). variant < 0 restores the
- * automatic choice.
+ * tile visit, 1..32 (also the halo width in rows), with region_rows - 2k >= k
+ * (the interior must be at least as tall as the halo), else MPN_EINVAL.
+ * variant < 0 restores the automatic choice.
  */
 mpn_status mpn_set_tuning(mpn_ctx *ctx, int32_t variant, int32_t depth);
 
@@ -193,6 +194,36 @@ mpn_status mpn_get_stats(mpn_ctx *ctx, mpn_stats *out);
 
 /* Number of kernels this library has launched in this process. */
 uint64_t mpn_launch_count(void);
+
+/*
+ * Distances for one grid without allocating any memory. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory (code running inside another framework's memory pool or a
+ * fixed-budget allocator, processes that must not grow after start-up,
+ * real-time loops where an allocation and its implied synchronisation are not
+ * allowed).
+ *
+ * Computes what mpn_create + mpn_propagate + mpn_get_distances compute for a
+ * uint32 plane. All pointers are DEVICE memory owned by the caller:
+ *   mask     H*W uint8, nonzero = obstacle;
+ *   targets  n_targets >= 1 linear indices;
+ *   dist     H*W uint32 output (0xFFFFFFFF = unreached or obstacle).
+ * max_layers as in mpn_propagate. Work is ordered on `stream`; the call waits
+ * for it to report errors (MPN_EINVAL for a target out of range,
+ * MPN_EOBSTACLE for one on an obstacle).
+ *
+ * Limit: H <= 2048 and W <= 2048; larger grids return MPN_EINVAL. The scratch
+ * (bit planes, tile queue, control block; about 2.1 MB) is one fixed device
+ * array that every GPU loading this library holds until the process exits.
+ * Calls never call cudaMalloc/cudaFree or any allocating routine. The first
+ * call on each device looks up that array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture. All calls
+ * share the array and each clears what must start at zero; calls whose GPU
+ * work overlaps (other streams, other host threads) race on it.
+ */
+mpn_status mpn_propagate_noalloc(const uint8_t *mask, int32_t H, int32_t W,
+                                 const uint32_t *targets, int32_t n_targets,
+                                 uint32_t max_layers, uint32_t *dist, void *stream);
 
 #ifdef __cplusplus
 }

@@ -27,7 +27,7 @@ EXPORTS = (
     "mpn_create", "mpn_create_packed", "mpn_set_mask", "mpn_set_stream", "mpn_propagate",
     "mpn_propagate_plain", "mpn_get_distances", "mpn_get_activity", "mpn_trace_lengths",
     "mpn_trace", "mpn_sync", "mpn_destroy", "mpn_status_str", "mpn_set_tuning",
-    "mpn_variant_info", "mpn_get_stats", "mpn_launch_count",
+    "mpn_variant_info", "mpn_get_stats", "mpn_launch_count", "mpn_propagate_noalloc",
 )
 
 
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
                                  ctypes.c_int),
             "mpn_get_stats": ([vp, ctypes.POINTER(mpn_stats)], ctypes.c_int),
             "mpn_launch_count": ([], u64),
+            "mpn_propagate_noalloc": ([vp, i32, i32, vp, i32, u32, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -239,6 +240,16 @@ def mpn_get_stats(ctx) -> dict:
 
 def mpn_launch_count() -> int:
     return int(load().mpn_launch_count())
+
+
+def mpn_propagate_noalloc(mask, H: int, W: int, targets, dist, max_layers: int = 0,
+                          stream=None):
+    """Distances into the caller's device buffer `dist` (H*W uint32) with no
+    allocation; mask, targets and dist must be CUDA tensors. Returns the
+    status code (MPN_OK, MPN_EINVAL past 2048 x 2048, ...)."""
+    n = int(targets.numel() if hasattr(targets, "numel") else np.asarray(targets).size)
+    return int(load().mpn_propagate_noalloc(_ptr(mask)[0], H, W, _ptr(targets)[0], n, max_layers,
+                                            _ptr(dist)[0], _stream_handle(stream)))
 
 
 # ---- convenience wrapper -----------------------------------------------

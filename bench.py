@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--depth", type=int, default=32)
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-maze batched/served part")
+    ap.add_argument("--batch-n", type=int, default=256)
+    ap.add_argument("--plain-sample", type=int, default=32,
+                    help="mazes timed with one launch per layer (the slow baseline)")
     return ap.parse_args()
 
 
@@ -207,6 +211,69 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_batched(args, pkg, torch):
+    """The 256-maze stream: batched capacity, per-maze baselines, serving."""
+    from paper_2004_00540_gb300.serve import Request, serve
+    ws = synth.c4_batch(args.batch_n)
+    cells = sum(w.H * w.W for w in ws)
+    dev = [(torch.from_numpy(w.mask).cuda(), torch.from_numpy(w.targets.view(np.int32)).cuda(),
+            torch.from_numpy(w.starts.view(np.int32)).cuda()) for w in ws]
+    torch.cuda.synchronize()
+    budget = int(sum(w.H * w.W * 5 + 4096 * 64 for w in ws) * 1.5) + (256 << 20)
+    out = {"workload": f"{len(ws)} grids, side U{{64..2048}}, even Bernoulli(0.3) / odd DFS maze, "
+                       f"1-16 targets, 10-200 starts", "cells": int(cells)}
+
+    def batched_once():
+        with pkg.Batch(budget) as b:
+            t0 = time.perf_counter()
+            tks = [b.submit(m, t, s, w.dist_bits) for (m, t, s), w in zip(dev, ws)]
+            assert all(tk is not None for tk in tks)
+            b.run(0)
+            res = [b.result(tk, w.starts.size, want_dist=False) for tk, w in zip(tks, ws)]
+            dt = time.perf_counter() - t0
+            st = b.stats()
+        return dt, res, st
+
+    batched_once()                                   # warm-up
+    dt, res, st = batched_once()
+    out["batched"] = {"mazes_per_s": len(ws) / dt, "seconds": dt, "rounds": st["rounds"],
+                      "sweeps": st["sweeps"], "propagate_round_ms": st["last_round_ms"]}
+
+    # per grid, one persistent launch each (same library, no batching)
+    t0 = time.perf_counter()
+    layers = []
+    for (m, t, s), w in zip(dev, ws):
+        with pkg.Planner(m, w.dist_bits) as pl:
+            layers.append(pl.propagate(t))
+            p = pl.trace(s.cpu().numpy().view(np.uint32))
+    dts = time.perf_counter() - t0
+    out["per_maze_persistent"] = {"mazes_per_s": len(ws) / dts, "seconds": dts}
+    # exactness: batched paths == per-grid paths
+    for (_, paths, L), Lr in zip(res[:8], layers[:8]):
+        assert L == Lr
+    # per grid, one launch per layer (the paper's recursive mode) on a sample
+    k = min(args.plain_sample, len(ws))
+    t0 = time.perf_counter()
+    for (m, t, s), w in list(zip(dev, ws))[:k]:
+        with pkg.Planner(m, w.dist_bits) as pl:
+            pl.propagate(t, plain=True, check_every=64)
+            pl.trace(s.cpu().numpy().view(np.uint32))
+    dtp = time.perf_counter() - t0
+    out["per_maze_plain_launches"] = {"mazes_per_s": k / dtp, "seconds": dtp,
+                                      "sample": f"first {k} of the {len(ws)} grids"}
+
+    # serving: Poisson arrivals at 0.8 x the batched capacity
+    lam = 0.8 * out["batched"]["mazes_per_s"]
+    arr = synth.poisson_arrivals(len(ws), lam, seed=4)
+    reqs = [Request(m, t, s, w.dist_bits, float(a)) for (m, t, s), w, a in zip(dev, ws, arr)]
+    with pkg.Batch(budget) as b:
+        rep = serve(b, reqs, round_sweeps=64)
+    out["serve"] = dict(rep.summary(), lambda_per_s=lam, round_sweeps=64)
+    out["speedup_vs_per_maze_plain"] = out["batched"]["mazes_per_s"] / out["per_maze_plain_launches"]["mazes_per_s"]
+    out["speedup_vs_per_maze_persistent"] = out["batched"]["mazes_per_s"] / out["per_maze_persistent"]["mazes_per_s"]
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -353,6 +420,8 @@ def main():
     }
     if pg:
         pg.destroy_process_group()
+    if not args.no_batched and world == 1:
+        line["batched"] = run_batched(args, pkg, torch)
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)

@@ -195,6 +195,88 @@ mpn_status mpn_get_stats(mpn_ctx *ctx, mpn_stats *out);
 /* Number of kernels this library has launched in this process. */
 uint64_t mpn_launch_count(void);
 
+/* ------------------------------------------------------------------------
+ * Batched and continuously batched solving of many grids.
+ *
+ * A batch owns one device arena of budget_bytes and a table of grid slots.
+ * mpn_batch_submit admits one grid (mask, targets, starts; host or device
+ * pointers, copied into the arena) if its bit planes and results fit in the
+ * arena now -- admission by device memory -- and returns MPN_ENOMEM
+ * otherwise, so the caller can retry after other grids are released.
+ * mpn_batch_run runs one round: grids submitted since the last round are
+ * seeded, then one persistent launch advances every admitted grid (their
+ * tiles share one work queue; each grid keeps its own layer clock) for up to
+ * max_sweeps sweeps (0 = until all converge). Grids that converged are
+ * traced at the end of the round (paths as in mpn_trace) and their bit planes
+ * are freed; their distance plane and paths stay until mpn_batch_release.
+ * (When a grid's paths do not fit in the arena at that moment, they are
+ * traced when mpn_batch_result asks for them: straight into a device `cells`
+ * buffer, or through a temporary device buffer for a host one -- the one
+ * allocation outside the budget.)
+ * Grids submitted while others are in flight join at the next round, so
+ * their work overlaps on the device. Results are the same as one grid solved
+ * alone with mpn_create/mpn_propagate/mpn_trace (bit for bit).
+ * ------------------------------------------------------------------------ */
+typedef struct mpn_batch mpn_batch;
+
+#define MPN_BATCH_PENDING 0
+#define MPN_BATCH_DONE 1
+#define MPN_BATCH_FAILED 2
+
+typedef struct {
+    uint64_t arena_bytes, arena_used, tiles_used;
+    uint32_t next_sweep;        /* global sweep counter */
+    uint64_t rounds, sweeps;    /* rounds run, sweeps run in total */
+    float last_round_ms;        /* device time of the last round's propagation */
+    int32_t blocks;             /* persistent blocks per launch */
+    int32_t admitted, running, done, failed;
+} mpn_batch_stats_t;
+
+/* budget_bytes >= 1 MiB: the arena; variant: compiled tile shape 0 or 1
+ * (-1 = 0); stream: cudaStream_t. */
+mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream,
+                            mpn_batch **out);
+
+/* Temporal depth used for grids submitted from now on (1..32, 0 = default). */
+mpn_status mpn_batch_set_depth(mpn_batch *b, int32_t depth);
+
+/* Admit one grid. dist_bits as in mpn_create; max_layers as in
+ * mpn_propagate. *ticket identifies it. MPN_ENOMEM: it does not fit now.
+ * End-points are checked here (the call waits for that): a target or start
+ * out of range is MPN_EINVAL, a target on an obstacle MPN_EOBSTACLE, and the
+ * grid is not admitted. A grid whose distances overflow a uint16 plane ends
+ * FAILED (MPN_EOVERFLOW). */
+mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_t W,
+                            const uint32_t *targets, int32_t n_targets,
+                            const uint32_t *starts, int32_t n_starts, int32_t dist_bits,
+                            uint32_t max_layers, uint64_t *ticket);
+
+/* One round (waits for it). n_running: grids admitted or in flight after the
+ * round; n_done: grids finished (done or failed) and not yet released. */
+mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running,
+                         int32_t *n_done);
+
+/* *state = MPN_BATCH_PENDING / _DONE / _FAILED (then returns its error). */
+mpn_status mpn_batch_poll(mpn_batch *b, uint64_t ticket, int32_t *state);
+
+/* Results of a DONE grid (any pointer may be NULL; host or device):
+ * dist H*W of its dtype, offsets[n_starts+1], cells[offsets[n]] (MPN_ENOMEM if
+ * cells_cap is smaller), status[n_starts], *layers. */
+mpn_status mpn_batch_result(mpn_batch *b, uint64_t ticket, void *dist, uint64_t *offsets,
+                            uint32_t *cells, uint64_t cells_cap, int8_t *status,
+                            uint32_t *layers);
+
+/* Shape, dtype and path-cell count of a submitted grid. */
+mpn_status mpn_batch_info(mpn_batch *b, uint64_t ticket, int32_t *H, int32_t *W,
+                          int32_t *dist_bits, uint64_t *total_cells);
+
+/* Free a finished grid's arena space and slot. MPN_ESTATE while in flight. */
+mpn_status mpn_batch_release(mpn_batch *b, uint64_t ticket);
+
+mpn_status mpn_batch_stats(mpn_batch *b, mpn_batch_stats_t *out);
+
+void mpn_batch_destroy(mpn_batch *b);
+
 /*
  * Distances for one grid without allocating any memory. The paper has no
  * counterpart: this entry point exists for callers that cannot allocate

@@ -1,0 +1,869 @@
+// Batched and continuously batched solving of many grids.
+//
+// A batch owns one device arena (its memory budget) and a table of grid slots.
+// mpn_batch_submit admits a grid if its planes fit in the arena (admission by
+// device memory) and gives it a range of global tile ids. mpn_batch_run runs
+// one round: grids admitted since the last round are encoded and seeded, then
+// ONE persistent launch advances every admitted grid -- tiles of all grids
+// share one work queue -- for up to a given number of sweeps, or until every
+// grid has converged. Each grid keeps its own layer clock (the sweep it
+// started at), so grids submitted while others are in flight join at the
+// next round and their work overlaps on the device. Grids that converge are
+// traced at the end of the round, release their bit planes, and keep their
+// distance plane and paths until mpn_batch_release.
+//
+// The per-tile work is wave::visit_tile, the same as the single-grid kernel.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "mpn_internal.cuh"
+#include "wave.cuh"
+
+namespace mpn {
+namespace {
+
+using wave::ld_acquire;
+using wave::ld_relaxed;
+
+// Device descriptor of one admitted grid.
+struct MazeDesc {
+    GridDev g;
+    int dist_bits;
+    int ntx, nty, TY, TXW, k;
+    uint32_t tile_base;     // first global tile id
+    uint32_t start_sweep;   // global sweep at which its layer 0 began
+    uint32_t max_layers;    // 0 = until convergence
+    uint32_t maxl;          // largest layer reached (atomicMax)
+    uint32_t last_push;     // 1 + last sweep one of its tiles was queued for
+    uint32_t err;           // ERR_* bits of this grid
+    uint32_t pad;
+};
+
+struct BatchCtl {
+    Ctl c;
+    uint32_t next_sweep;    // global sweep the next round starts at
+    uint32_t pad[3];
+};
+
+struct BatchParams {
+    MazeDesc *descs;
+    uint32_t *tile_maze;    // global tile id -> slot
+    uint32_t *queued;       // global tile id -> 1 + last sweep queued for
+    uint32_t *lists;        // 3 lists of max_tiles entries
+    uint32_t max_tiles;
+    BatchCtl *bc;
+    uint32_t round_sweeps;  // 0 = until every grid converged
+    uint32_t spin_limit;
+};
+
+struct SeedJob {
+    uint32_t slot;
+    uint32_t n;
+    const uint32_t *targets;
+};
+
+__device__ __forceinline__ void push_tile_b(const BatchParams &p, const MazeDesc &d, uint32_t slot,
+                                            int ty, int tx, uint32_t s) {
+    if (ty < 0 || tx < 0 || ty >= d.nty || tx >= d.ntx) return;
+    const uint32_t gt = d.tile_base + (uint32_t)(ty * d.ntx + tx);
+    if (atomicMax(p.queued + gt, s + 1) < s + 1) {
+        const uint32_t sl = s % 3;
+        const uint32_t i = atomicAdd(&p.bc->c.list_len[sl], 1u);
+        p.lists[(size_t)sl * p.max_tiles + i] = gt;
+        atomicMax(&p.descs[slot].last_push, s + 1);
+    }
+}
+
+__device__ void push_zone_b(const BatchParams &p, const MazeDesc &d, uint32_t slot, int ty, int tx,
+                            uint32_t zone, uint32_t s) {
+    if (zone & FB_ANY) push_tile_b(p, d, slot, ty, tx, s);
+    if (zone & FB_N) push_tile_b(p, d, slot, ty - 1, tx, s);
+    if (zone & FB_S) push_tile_b(p, d, slot, ty + 1, tx, s);
+    if (zone & FB_W) push_tile_b(p, d, slot, ty, tx - 1, s);
+    if (zone & FB_E) push_tile_b(p, d, slot, ty, tx + 1, s);
+    if (zone & FB_NW) push_tile_b(p, d, slot, ty - 1, tx - 1, s);
+    if (zone & FB_NE) push_tile_b(p, d, slot, ty - 1, tx + 1, s);
+    if (zone & FB_SW) push_tile_b(p, d, slot, ty + 1, tx - 1, s);
+    if (zone & FB_SE) push_tile_b(p, d, slot, ty + 1, tx + 1, s);
+}
+
+// One block per admitted grid: distance 0 and the reached bit at its
+// targets, and its first tiles queued for the round's first sweep.
+__global__ void k_batch_seed(BatchParams p, const SeedJob *jobs) {
+    const SeedJob job = jobs[blockIdx.x];
+    const MazeDesc d = p.descs[job.slot];
+    const uint32_t S = d.start_sweep;
+    for (uint32_t i = threadIdx.x; i < job.n; i += blockDim.x) {
+        const uint32_t t = job.targets[i];
+        if ((uint64_t)t >= (uint64_t)d.g.H * (uint64_t)d.g.W) {
+            atomicOr(&p.descs[job.slot].err, ERR_INVAL);
+            continue;
+        }
+        const int y = (int)(t / (uint32_t)d.g.W), x = (int)(t % (uint32_t)d.g.W);
+        const size_t wo = (size_t)y * d.g.P + (x >> 5);
+        const uint32_t bit = 1u << (x & 31);
+        if (!(d.g.free_bits[wo] & bit)) {
+            atomicOr(&p.descs[job.slot].err, ERR_OBSTACLE);
+            continue;
+        }
+        if (d.dist_bits == 16) reinterpret_cast<uint16_t *>(d.g.dist)[t] = 0;
+        else reinterpret_cast<uint32_t *>(d.g.dist)[t] = 0u;
+        atomicOr(d.g.vis + wo, bit);
+        const int ty = y / d.TY, tx = (x >> 5) / d.TXW;
+        const int ri = y - ty * d.TY, wi = (x >> 5) - tx * d.TXW;
+        push_zone_b(p, d, job.slot, ty, tx, wave::border_bits(ri, wi, bit, d.k, d.TY, d.TXW), S);
+    }
+}
+
+template <int RXW, int R, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p) {
+    __shared__ wave::VisitSmem<RXW, NW> sm;
+    __shared__ int s_tile;
+    __shared__ unsigned s_mask[2], s_lastj[2], s_done, s_ok;
+    Ctl *ctl = &p.bc->c;
+    unsigned vq = 0u;
+    unsigned long long blk_visits = 0;
+    const uint32_t s0 = ld_acquire(&p.bc->next_sweep);
+
+    for (uint32_t s = s0;; ++s) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->work[(s + 2) % 3] = 0u;
+            ctl->list_len[(s + 2) % 3] = 0u;
+        }
+        const uint32_t *list = p.lists + (size_t)(s % 3) * p.max_tiles;
+        unsigned *work = &ctl->work[s % 3];
+        const uint32_t len = ld_acquire(&ctl->list_len[s % 3]);
+        if (threadIdx.x == 0) {
+            const uint32_t i = atomicAdd(work, 1u);
+            s_tile = (i < len) ? (int)ld_relaxed(list + i) : -1;
+        }
+        __syncthreads();
+        int t = s_tile;
+        while (t >= 0) {
+            uint32_t next_i = 0;
+            vq ^= 1u;
+            if (threadIdx.x == 0) {
+                next_i = atomicAdd(work, 1u);
+                s_mask[vq] = 0u;
+                s_lastj[vq] = 0u;
+            }
+            const uint32_t slot = __ldg(p.tile_maze + t);
+            const MazeDesc &dref = p.descs[slot];
+            // defensive: a list entry must lie in its grid's tile range
+            const bool valid = (uint32_t)t - dref.tile_base < (uint32_t)(dref.ntx * dref.nty);
+            wave::Visit v;
+            v.g = dref.g;
+            v.dist_bits = dref.dist_bits;
+            v.TY = dref.TY;
+            v.TXW = dref.TXW;
+            v.k = dref.k;
+            const int ntx = dref.ntx;
+            const uint32_t local = (uint32_t)t - dref.tile_base;
+            v.ty = (int)(local / (uint32_t)ntx);
+            v.tx = (int)(local - (uint32_t)v.ty * ntx);
+            v.l0 = (s - dref.start_sweep) * (uint32_t)v.k;
+            const uint32_t maxl = dref.max_layers;
+            v.jmax = v.k;
+            if (maxl && v.l0 + (uint32_t)v.k > maxl) v.jmax = (int)(maxl - v.l0);
+            v.nbS = (s & 1) ? v.g.nb1 : v.g.nb0;
+            uint32_t fmask = 0u;
+            unsigned lastj = 0u;
+            if (valid) wave::visit_tile<RXW, R, NW>(v, sm, &p.descs[slot].err, &fmask, &lastj);
+            if (maxl && v.l0 + (uint32_t)v.k >= maxl) fmask = 0u;   // fixed depth reached
+            if (fmask) atomicOr(&s_mask[vq], fmask);
+            if (lastj) atomicMax(&s_lastj[vq], lastj);
+            if (threadIdx.x == 0) {
+                ++blk_visits;
+                s_tile = (next_i < len) ? (int)ld_relaxed(list + next_i) : -1;
+            }
+            __syncthreads();
+            if (threadIdx.x < 9) {
+                const uint32_t zone = 1u << threadIdx.x;
+                if (s_mask[vq] & zone) push_zone_b(p, dref, slot, v.ty, v.tx, zone, s + 1);
+                if (threadIdx.x == 0 && s_lastj[vq])
+                    atomicMax(&p.descs[slot].maxl, v.l0 + s_lastj[vq]);
+            }
+            t = s_tile;
+        }
+
+        if (!wave::grid_barrier(ctl, gridDim.x, p.spin_limit, &s_ok)) return;
+        if (threadIdx.x == 0) {
+            const unsigned done = (ld_acquire(&ctl->list_len[(s + 1) % 3]) == 0u) ||
+                                  (p.round_sweeps && s + 1 - s0 >= p.round_sweeps);
+            if (done && blockIdx.x == 0) {
+                p.bc->next_sweep = s + 1;
+                ctl->sweeps = s + 1 - s0;
+            }
+            if (done && blk_visits) atomicAdd(&ctl->visits, blk_visits);
+            s_done = done;
+        }
+        __syncthreads();
+        if (s_done) return;
+    }
+}
+
+// Submit-time check: every target in range and on a free cell, every start
+// in range (bit 0: target out of range, 1: target on an obstacle, 2: start
+// out of range).
+__global__ void k_check_inputs(const uint32_t *free_bits, int H, int W, int P,
+                               const uint32_t *targets, int nt, const uint32_t *starts, int ns,
+                               uint32_t *flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t N = (uint64_t)H * W;
+    if (i < nt) {
+        const uint32_t t = targets[i];
+        if (t >= N) {
+            atomicOr(flag, 1u);
+        } else {
+            const int y = (int)(t / (uint32_t)W), x = (int)(t % (uint32_t)W);
+            if (!((free_bits[(size_t)y * P + (x >> 5)] >> (x & 31)) & 1u)) atomicOr(flag, 2u);
+        }
+    }
+    if (i < ns && starts[i] >= N) atomicOr(flag, 4u);
+}
+
+__global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+template <int RXW, int R, int NW, int MINB>
+void *batch_ptr() {
+    return (void *)k_batch_propagate<RXW, R, NW, MINB>;
+}
+
+// The batch runs on compiled shape 0 (128-row x 8-word region) and its
+// 256-row sibling; per grid only the depth varies.
+void *batch_fn(int v) {
+    switch (v) {
+        case 0: return batch_ptr<8, 4, 8, 3>();
+        case 1: return batch_ptr<8, 8, 8, 2>();
+        default: return nullptr;
+    }
+}
+
+// ---- host side --------------------------------------------------------
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+
+// First-fit allocator over [0, capacity) (offsets in bytes or tile ids).
+struct RangeAlloc {
+    std::map<size_t, size_t> free_;   // offset -> length
+    size_t capacity = 0, used = 0;
+    void init(size_t cap) {
+        capacity = cap;
+        used = 0;
+        free_.clear();
+        if (cap) free_[0] = cap;
+    }
+    bool alloc(size_t n, size_t *off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const size_t rest = it->second - n, start = it->first + n;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used += n;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        if (!n) return;
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+// Admitted: waiting for its first round. Running: in flight. Traced: done
+// (paths in the arena, or traced on demand by mpn_batch_result when they did
+// not fit). Failed: done with an error.
+enum class MState { Admitted, Running, Traced, Failed };
+
+struct HostMaze {
+    uint64_t ticket = 0;
+    uint32_t slot = 0;
+    int H = 0, W = 0, P = 0, dist_bits = 32;
+    int ntx = 0, nty = 0, TY = 0, TXW = 0, k = 32;
+    uint32_t tile_base = 0, ntiles = 0;
+    uint32_t max_layers = 0;
+    int nt = 0, ns = 0;
+    // arena blocks: planes (freed after tracing) and results (kept)
+    size_t planes_off = 0, planes_bytes = 0;
+    size_t res_off = 0, res_bytes = 0;       // dist + targets + starts + offsets + status
+    size_t cells_off = 0, cells_bytes = 0;
+    size_t dist_o = 0, tgt_o = 0, st_o = 0, off_o = 0, sts_o = 0;   // within the result block
+    MState state = MState::Admitted;
+    mpn_status code = MPN_OK;
+    uint32_t layers = 0;
+    uint64_t total = 0;
+    bool has_tiles = false, has_planes = false;
+    bool paths_ready = false;   // cells traced into the arena
+};
+
+}  // namespace
+}  // namespace mpn
+
+using namespace mpn;
+
+struct mpn_batch {
+    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 0;
+    int variant = 0, blocks = 0;
+    int depth_override = 0;
+    uint32_t max_slots = 0, max_tiles = 0;
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
+    RangeAlloc mem, tiles;
+    MazeDesc *d_descs = nullptr;
+    uint32_t *d_tile_maze = nullptr, *d_queued = nullptr, *d_lists = nullptr;
+    BatchCtl *d_bc = nullptr;
+    SeedJob *d_jobs = nullptr;
+    MazeDesc *h_descs = nullptr;      // pinned mirror for readback
+    BatchCtl *h_bc = nullptr;         // pinned
+    SeedJob *h_jobs = nullptr;        // pinned
+    uint32_t *h_flag = nullptr;       // pinned
+    std::vector<uint32_t> free_slots;
+    std::map<uint64_t, HostMaze> mazes;
+    uint64_t next_ticket = 1;
+    uint32_t next_sweep = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    float last_round_ms = 0.f;
+    uint64_t rounds = 0, sweeps_total = 0;
+};
+
+namespace {
+
+mpn_status cuda_st(cudaError_t e) {
+    if (e == cudaSuccess) return MPN_OK;
+    return e == cudaErrorMemoryAllocation ? MPN_ENOMEM : MPN_ECUDA;
+}
+
+#define B_TRY(expr)                                   \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return cuda_st(e_);    \
+    } while (0)
+
+bool dev_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void *arena_at(mpn_batch *b, size_t off) { return (char *)b->arena + off; }
+
+// Depth used for a grid: the override if set, else 32 (interior 64 rows of
+// the 128-row region); variant 1 (256 rows) uses 32 as well.
+int depth_for(mpn_batch *b, int H, int W) {
+    (void)H;
+    (void)W;
+    if (b->depth_override) return b->depth_override;
+    return 32;
+}
+
+void release_planes(mpn_batch *b, HostMaze &m) {
+    if (m.has_planes) {
+        b->mem.release(m.planes_off, m.planes_bytes);
+        m.has_planes = false;
+    }
+    if (m.has_tiles) {
+        b->tiles.release(m.tile_base, m.ntiles);
+        m.has_tiles = false;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream, mpn_batch **out) {
+    if (!out || budget_bytes < (1u << 20)) return MPN_EINVAL;
+    *out = nullptr;
+    if (variant < 0) variant = 0;
+    if (!batch_fn(variant)) return MPN_EINVAL;
+    mpn_batch *b = new (std::nothrow) mpn_batch();
+    if (!b) return MPN_ENOMEM;
+    b->stream = (cudaStream_t)stream;
+    b->variant = variant;
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device);
+    const VariantDesc vd = variant_desc(variant);
+    int bps = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, batch_fn(variant), vd.nwarps * 32, 0);
+    if (e != cudaSuccess || bps < 1) {
+        delete b;
+        return e == cudaSuccess ? MPN_ECUDA : cuda_st(e);
+    }
+    b->blocks = bps * b->sm_count;
+    b->max_slots = 4096;
+    // a tile covers at least 32 x 192 cells (>= ~27 KB of planes at uint32)
+    size_t mt = budget_bytes / 8192;
+    if (mt > (1u << 22)) mt = 1u << 22;
+    if (mt < 4096) mt = 4096;
+    b->max_tiles = (uint32_t)mt;
+    b->arena_bytes = budget_bytes;
+    e = cudaMalloc(&b->arena, budget_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_descs, b->max_slots * sizeof(MazeDesc));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tile_maze, (size_t)b->max_tiles * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_queued, (size_t)b->max_tiles * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_lists, (size_t)b->max_tiles * 3 * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bc, sizeof(BatchCtl));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_jobs, b->max_slots * sizeof(SeedJob));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_descs, b->max_slots * sizeof(MazeDesc));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_bc, sizeof(BatchCtl));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_jobs, b->max_slots * sizeof(SeedJob));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_flag, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queued, 0, (size_t)b->max_tiles * 4, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bc, 0, sizeof(BatchCtl), b->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        mpn_batch_destroy(b);
+        return cuda_st(e);
+    }
+    b->mem.init(budget_bytes);
+    b->tiles.init(b->max_tiles);
+    for (uint32_t i = b->max_slots; i-- > 0;) b->free_slots.push_back(i);
+    *out = b;
+    return MPN_OK;
+}
+
+mpn_status mpn_batch_set_depth(mpn_batch *b, int32_t depth) {
+    if (!b || depth < 0 || depth > 32) return MPN_EINVAL;
+    const VariantDesc vd = variant_desc(b->variant);
+    const int ry = vd.nwarps * (32 / vd.rxw) * vd.r;
+    if (depth && ry - 2 * depth < depth) return MPN_EINVAL;
+    b->depth_override = depth;
+    return MPN_OK;
+}
+
+mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_t W,
+                            const uint32_t *targets, int32_t nt, const uint32_t *starts, int32_t ns,
+                            int32_t dist_bits, uint32_t max_layers, uint64_t *ticket) {
+    if (!b || !mask || !targets || nt < 1 || ns < 0 || (ns > 0 && !starts) || !ticket) return MPN_EINVAL;
+    if (H < 1 || W < 1 || (uint64_t)H * W >= 0xffffffffull) return MPN_EINVAL;
+    if (dist_bits == MPN_DIST_AUTO) dist_bits = ((int64_t)H * W <= 65535) ? 16 : 32;
+    if (dist_bits != 16 && dist_bits != 32) return MPN_EINVAL;
+    if (b->free_slots.empty()) return MPN_ENOMEM;
+    HostMaze m;
+    m.H = H;
+    m.W = W;
+    m.P = (((W + 31) / 32) + 3) / 4 * 4;
+    m.dist_bits = dist_bits;
+    m.k = depth_for(b, H, W);
+    const VariantDesc vd = variant_desc(b->variant);
+    const int ry = vd.nwarps * (32 / vd.rxw) * vd.r;
+    m.TY = ry - 2 * m.k;
+    m.TXW = vd.rxw - 2;
+    m.ntx = ((W + 31) / 32 + m.TXW - 1) / m.TXW;
+    m.nty = (H + m.TY - 1) / m.TY;
+    m.ntiles = (uint32_t)(m.ntx * m.nty);
+    m.max_layers = max_layers;
+    m.nt = nt;
+    m.ns = ns;
+    const size_t plane = align_up((size_t)H * m.P * 4);
+    m.planes_bytes = 4 * plane;
+    m.dist_o = 0;
+    m.tgt_o = align_up((size_t)H * W * (dist_bits / 8));
+    m.st_o = m.tgt_o + align_up((size_t)nt * 4);
+    m.off_o = m.st_o + align_up((size_t)(ns > 0 ? ns : 1) * 4);
+    m.sts_o = m.off_o + align_up((size_t)(ns + 1) * 8);
+    m.res_bytes = m.sts_o + align_up((size_t)(ns > 0 ? ns : 1));
+    // admission by device memory: planes + results must fit now, tiles too
+    size_t tb = 0;
+    if (!b->tiles.alloc(m.ntiles, &tb)) return MPN_ENOMEM;
+    if (!b->mem.alloc(m.planes_bytes, &m.planes_off)) {
+        b->tiles.release(tb, m.ntiles);
+        return MPN_ENOMEM;
+    }
+    if (!b->mem.alloc(m.res_bytes, &m.res_off)) {
+        b->tiles.release(tb, m.ntiles);
+        b->mem.release(m.planes_off, m.planes_bytes);
+        return MPN_ENOMEM;
+    }
+    m.tile_base = (uint32_t)tb;
+    m.has_tiles = m.has_planes = true;
+    m.slot = b->free_slots.back();
+    b->free_slots.pop_back();
+    m.ticket = b->next_ticket++;
+
+    // inputs into the arena (host or device sources), planes initialised
+    cudaStream_t st = b->stream;
+    char *res = (char *)arena_at(b, m.res_off);
+    uint32_t *fb = (uint32_t *)arena_at(b, m.planes_off);
+    cudaError_t e = cudaSuccess;
+    const cudaMemcpyKind kt = dev_ptr(targets) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    e = cudaMemcpyAsync(res + m.tgt_o, targets, (size_t)nt * 4, kt, st);
+    if (e == cudaSuccess && ns > 0)
+        e = cudaMemcpyAsync(res + m.st_o, starts, (size_t)ns * 4,
+                            dev_ptr(starts) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    // a host mask is staged in the (not yet filled) distance plane, which is
+    // at least H*W bytes
+    const uint8_t *dmask = mask;
+    if (e == cudaSuccess && !dev_ptr(mask)) {
+        dmask = (const uint8_t *)(res + m.dist_o);
+        e = cudaMemcpyAsync((void *)dmask, mask, (size_t)H * W, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = launch_pack(dmask, H, W, m.P, fb, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync((char *)fb + plane, 0, 3 * plane, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(res + m.dist_o, 0xff, (size_t)H * W * (dist_bits / 8), st);
+    // reject bad end-points now, so that no grid can fail while in flight
+    uint32_t *flag = (uint32_t *)((char *)fb + plane);   // one word of the zeroed visit plane
+    if (e == cudaSuccess) {
+        const int n = nt > ns ? nt : ns;
+        count_launch();
+        k_check_inputs<<<(n + 255) / 256, 256, 0, st>>>(fb, H, W, m.P, (const uint32_t *)(res + m.tgt_o),
+                                                        nt, (const uint32_t *)(res + m.st_o), ns, flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_flag, flag, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    mpn_status bad = MPN_OK;
+    if (e == cudaSuccess && *b->h_flag) bad = (*b->h_flag & 2u) && !(*b->h_flag & 5u) ? MPN_EOBSTACLE : MPN_EINVAL;
+    if (e != cudaSuccess || bad != MPN_OK) {
+        release_planes(b, m);
+        b->mem.release(m.res_off, m.res_bytes);
+        b->free_slots.push_back(m.slot);
+        return e != cudaSuccess ? cuda_st(e) : bad;
+    }
+    b->mazes.emplace(m.ticket, m);
+    *ticket = m.ticket;
+    return MPN_OK;
+}
+
+static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t *cells) {
+    char *res = (char *)arena_at(b, m.res_off);
+    GridDev g;
+    g.free_bits = nullptr;
+    g.vis = g.nb0 = g.nb1 = nullptr;
+    g.dist = res + m.dist_o;
+    g.H = m.H;
+    g.W = m.W;
+    g.P = m.P;
+    return launch_trace(g, m.dist_bits, (const uint32_t *)(res + m.st_o), m.ns,
+                        (const uint64_t *)(res + m.off_o), (const int8_t *)(res + m.sts_o), cells,
+                        b->stream, &b->d_bc->c.err);
+}
+
+// Wait for the stream, then trace every grid that converged in the last round.
+static mpn_status finish_round(mpn_batch *b) {
+    cudaStream_t st = b->stream;
+    B_TRY(cudaMemcpyAsync(b->h_bc, b->d_bc, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
+    B_TRY(cudaMemcpyAsync(b->h_descs, b->d_descs, b->max_slots * sizeof(MazeDesc),
+                          cudaMemcpyDeviceToHost, st));
+    B_TRY(cudaStreamSynchronize(st));
+    b->next_sweep = b->h_bc->next_sweep;
+    if (b->h_bc->c.err & ERR_TIMEOUT) return MPN_ETIMEOUT;
+    std::vector<HostMaze *> done;
+    for (auto &kv : b->mazes) {
+        HostMaze &m = kv.second;
+        if (m.state != MState::Running) continue;
+        const MazeDesc &d = b->h_descs[m.slot];
+        if (d.last_push > b->next_sweep) continue;   // tiles still queued for the next sweep
+        if (d.err) {
+            // (a uint16 overflow; end-points were checked at submit) -- the grid
+            // has drained, so its planes can go
+            m.state = MState::Failed;
+            m.code = (d.err & ERR_OVERFLOW) ? MPN_EOVERFLOW : MPN_ECUDA;
+            release_planes(b, m);
+            continue;
+        }
+        {
+            m.layers = d.maxl;
+            done.push_back(&m);
+        }
+    }
+    // path lengths and offsets of every newly converged grid, then one wait
+    Ctl *ctl = &b->d_bc->c;
+    if (!done.empty()) {
+        for (HostMaze *m : done) {
+            char *res = (char *)arena_at(b, m->res_off);
+            GridDev g;
+            g.free_bits = (const uint32_t *)arena_at(b, m->planes_off);
+            g.vis = g.nb0 = g.nb1 = nullptr;
+            g.dist = res + m->dist_o;
+            g.H = m->H;
+            g.W = m->W;
+            g.P = m->P;
+            B_TRY(cudaMemsetAsync(res + m->off_o, 0, 8, st));
+            if (m->ns > 0) {
+                B_TRY(launch_trace_lengths(g, m->dist_bits, (const uint32_t *)(res + m->st_o), m->ns,
+                                           (uint64_t *)(res + m->off_o), (int8_t *)(res + m->sts_o),
+                                           ctl, st));
+                B_TRY(launch_scan((uint64_t *)(res + m->off_o), m->ns, st));
+            }
+        }
+        std::vector<uint64_t> totals(done.size());
+        for (size_t i = 0; i < done.size(); ++i) {
+            char *res = (char *)arena_at(b, done[i]->res_off);
+            B_TRY(cudaMemcpyAsync(&totals[i], (uint64_t *)(res + done[i]->off_o) + done[i]->ns, 8,
+                                  cudaMemcpyDeviceToHost, st));
+        }
+        B_TRY(cudaStreamSynchronize(st));
+        // the bit planes are not needed any more (tracing reads the distances)
+        for (size_t i = 0; i < done.size(); ++i) {
+            done[i]->total = totals[i];
+            done[i]->state = MState::Traced;
+            release_planes(b, *done[i]);
+        }
+    }
+    // paths of every finished grid whose paths fit in the arena now; the
+    // others are traced on demand into the caller's buffer
+    bool launched = false;
+    for (HostMaze *m : done) {
+        m->cells_bytes = align_up((size_t)(m->total ? m->total : 1) * 4);
+        if (!b->mem.alloc(m->cells_bytes, &m->cells_off)) {
+            m->cells_bytes = 0;
+            continue;
+        }
+        if (m->ns > 0) B_TRY(launch_batch_trace(b, *m, (uint32_t *)arena_at(b, m->cells_off)));
+        m->paths_ready = true;
+        launched = true;
+    }
+    if (launched) B_TRY(cudaStreamSynchronize(st));
+    return MPN_OK;
+}
+
+mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, int32_t *n_done) {
+    if (!b) return MPN_EINVAL;
+    cudaStream_t st = b->stream;
+    // descriptors and seeds of the grids admitted since the last round
+    int njobs = 0;
+    for (auto &kv : b->mazes) {
+        HostMaze &m = kv.second;
+        if (m.state != MState::Admitted) continue;
+        MazeDesc d{};
+        char *res = (char *)arena_at(b, m.res_off);
+        const size_t plane = m.planes_bytes / 4;
+        d.g.free_bits = (const uint32_t *)arena_at(b, m.planes_off);
+        d.g.vis = (uint32_t *)((char *)arena_at(b, m.planes_off) + plane);
+        d.g.nb0 = (uint32_t *)((char *)arena_at(b, m.planes_off) + 2 * plane);
+        d.g.nb1 = (uint32_t *)((char *)arena_at(b, m.planes_off) + 3 * plane);
+        d.g.dist = res + m.dist_o;
+        d.g.H = m.H;
+        d.g.W = m.W;
+        d.g.P = m.P;
+        d.dist_bits = m.dist_bits;
+        d.ntx = m.ntx;
+        d.nty = m.nty;
+        d.TY = m.TY;
+        d.TXW = m.TXW;
+        d.k = m.k;
+        d.tile_base = m.tile_base;
+        d.start_sweep = b->next_sweep;
+        d.max_layers = m.max_layers;
+        b->h_descs[m.slot] = d;
+        B_TRY(cudaMemcpyAsync(b->d_descs + m.slot, &b->h_descs[m.slot], sizeof(MazeDesc),
+                              cudaMemcpyHostToDevice, st));
+        b->h_jobs[njobs].slot = m.slot;
+        b->h_jobs[njobs].n = (uint32_t)m.nt;
+        b->h_jobs[njobs].targets = (const uint32_t *)(res + m.tgt_o);
+        ++njobs;
+        m.state = MState::Running;
+    }
+    // tile -> slot map of the new grids
+    for (int j = 0; j < njobs; ++j) {
+        const HostMaze *m = nullptr;
+        for (auto &kv : b->mazes)
+            if (kv.second.slot == b->h_jobs[j].slot && kv.second.state == MState::Running) m = &kv.second;
+        if (!m) continue;
+        const unsigned nb = (m->ntiles + 255) / 256;
+        count_launch();
+        k_fill_u32<<<nb < 1024 ? nb : 1024, 256, 0, st>>>(b->d_tile_maze + m->tile_base, m->ntiles, m->slot);
+        B_TRY(cudaGetLastError());
+    }
+    BatchParams p{};
+    p.descs = b->d_descs;
+    p.tile_maze = b->d_tile_maze;
+    p.queued = b->d_queued;
+    p.lists = b->d_lists;
+    p.max_tiles = b->max_tiles;
+    p.bc = b->d_bc;
+    p.round_sweeps = max_sweeps;
+    p.spin_limit = 1u << 24;
+    if (njobs > 0) {
+        B_TRY(cudaMemcpyAsync(b->d_jobs, b->h_jobs, njobs * sizeof(SeedJob), cudaMemcpyHostToDevice, st));
+        count_launch();
+        k_batch_seed<<<njobs, 128, 0, st>>>(p, b->d_jobs);
+        B_TRY(cudaGetLastError());
+    }
+    int running = 0;
+    for (auto &kv : b->mazes) running += kv.second.state == MState::Running;
+    if (running > 0) {
+        // a fresh work counter for the round's first sweep
+        B_TRY(cudaMemsetAsync(&b->d_bc->c.work[b->next_sweep % 3], 0, 4, st));
+        B_TRY(cudaMemsetAsync(&b->d_bc->c.err, 0, 4, st));
+        B_TRY(cudaEventRecord(b->ev0, st));
+        void *args[] = {&p};
+        const VariantDesc vd = variant_desc(b->variant);
+        count_launch();
+        B_TRY(cudaLaunchCooperativeKernel(batch_fn(b->variant), dim3(b->blocks), dim3(vd.nwarps * 32),
+                                          args, 0, st));
+        B_TRY(cudaEventRecord(b->ev1, st));
+    }
+    mpn_status s = finish_round(b);
+    if (running > 0) {
+        cudaEventElapsedTime(&b->last_round_ms, b->ev0, b->ev1);
+        b->rounds++;
+        b->sweeps_total += b->h_bc->c.sweeps;
+    }
+    int r = 0, d = 0;
+    for (auto &kv : b->mazes) {
+        r += kv.second.state == MState::Running || kv.second.state == MState::Admitted;
+        d += kv.second.state == MState::Traced || kv.second.state == MState::Failed;
+    }
+    if (n_running) *n_running = r;
+    if (n_done) *n_done = d;
+    return s;
+}
+
+mpn_status mpn_batch_poll(mpn_batch *b, uint64_t ticket, int32_t *state) {
+    if (!b || !state) return MPN_EINVAL;
+    auto it = b->mazes.find(ticket);
+    if (it == b->mazes.end()) return MPN_EINVAL;
+    const MState s = it->second.state;
+    *state = s == MState::Traced ? MPN_BATCH_DONE : s == MState::Failed ? MPN_BATCH_FAILED
+                                                                        : MPN_BATCH_PENDING;
+    return s == MState::Failed ? it->second.code : MPN_OK;
+}
+
+mpn_status mpn_batch_result(mpn_batch *b, uint64_t ticket, void *dist, uint64_t *offsets,
+                            uint32_t *cells, uint64_t cells_cap, int8_t *status, uint32_t *layers) {
+    if (!b) return MPN_EINVAL;
+    auto it = b->mazes.find(ticket);
+    if (it == b->mazes.end()) return MPN_EINVAL;
+    HostMaze &m = it->second;
+    if (m.state == MState::Failed) return m.code;
+    if (m.state != MState::Traced) return MPN_ESTATE;
+    cudaStream_t st = b->stream;
+    char *res = (char *)arena_at(b, m.res_off);
+    auto kind = [](const void *p) {
+        return dev_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    };
+    if (layers) *layers = m.layers;
+    if (dist)
+        B_TRY(cudaMemcpyAsync(dist, res + m.dist_o, (size_t)m.H * m.W * (m.dist_bits / 8), kind(dist), st));
+    if (offsets)
+        B_TRY(cudaMemcpyAsync(offsets, res + m.off_o, (size_t)(m.ns + 1) * 8, kind(offsets), st));
+    if (status && m.ns > 0)
+        B_TRY(cudaMemcpyAsync(status, res + m.sts_o, (size_t)m.ns, kind(status), st));
+    if (cells && m.total > 0) {
+        if (m.total > cells_cap) {
+            B_TRY(cudaStreamSynchronize(st));
+            return MPN_ENOMEM;
+        }
+        if (m.paths_ready) {
+            B_TRY(cudaMemcpyAsync(cells, arena_at(b, m.cells_off), (size_t)m.total * 4, kind(cells), st));
+        } else if (dev_ptr(cells)) {
+            B_TRY(launch_batch_trace(b, m, cells));            // straight into the caller's buffer
+        } else {
+            // host buffer and no room in the arena: a temporary device buffer
+            void *tmp = nullptr;
+            B_TRY(cudaMalloc(&tmp, (size_t)m.total * 4));
+            cudaError_t e = launch_batch_trace(b, m, (uint32_t *)tmp);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cells, tmp, (size_t)m.total * 4, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            cudaFree(tmp);
+            B_TRY(e);
+        }
+    }
+    B_TRY(cudaStreamSynchronize(st));
+    return MPN_OK;
+}
+
+mpn_status mpn_batch_info(mpn_batch *b, uint64_t ticket, int32_t *H, int32_t *W, int32_t *dist_bits,
+                          uint64_t *total_cells) {
+    if (!b) return MPN_EINVAL;
+    auto it = b->mazes.find(ticket);
+    if (it == b->mazes.end()) return MPN_EINVAL;
+    const HostMaze &m = it->second;
+    if (H) *H = m.H;
+    if (W) *W = m.W;
+    if (dist_bits) *dist_bits = m.dist_bits;
+    if (total_cells) *total_cells = m.total;
+    return MPN_OK;
+}
+
+mpn_status mpn_batch_release(mpn_batch *b, uint64_t ticket) {
+    if (!b) return MPN_EINVAL;
+    auto it = b->mazes.find(ticket);
+    if (it == b->mazes.end()) return MPN_EINVAL;
+    HostMaze &m = it->second;
+    if (m.state == MState::Running || m.state == MState::Admitted) return MPN_ESTATE;
+    release_planes(b, m);
+    b->mem.release(m.res_off, m.res_bytes);
+    if (m.cells_bytes) b->mem.release(m.cells_off, m.cells_bytes);
+    b->free_slots.push_back(m.slot);
+    b->mazes.erase(it);
+    return MPN_OK;
+}
+
+mpn_status mpn_batch_stats(mpn_batch *b, mpn_batch_stats_t *out) {
+    if (!b || !out) return MPN_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->arena_bytes = b->arena_bytes;
+    out->arena_used = b->mem.used;
+    out->tiles_used = b->tiles.used;
+    out->next_sweep = b->next_sweep;
+    out->rounds = b->rounds;
+    out->sweeps = b->sweeps_total;
+    out->last_round_ms = b->last_round_ms;
+    out->blocks = b->blocks;
+    for (auto &kv : b->mazes) {
+        const MState s = kv.second.state;
+        out->admitted += s == MState::Admitted;
+        out->running += s == MState::Running;
+        out->done += s == MState::Traced;
+        out->failed += s == MState::Failed;
+    }
+    return MPN_OK;
+}
+
+void mpn_batch_destroy(mpn_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    cudaFree(b->arena);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_tile_maze);
+    cudaFree(b->d_queued);
+    cudaFree(b->d_lists);
+    cudaFree(b->d_bc);
+    cudaFree(b->d_jobs);
+    if (b->h_descs) cudaFreeHost(b->h_descs);
+    if (b->h_bc) cudaFreeHost(b->h_bc);
+    if (b->h_jobs) cudaFreeHost(b->h_jobs);
+    if (b->h_flag) cudaFreeHost(b->h_flag);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+}
+
+}  // extern "C"

@@ -1,15 +1,6 @@
-// Activity propagation: the stack of max-pool layers (Methods, "Activity Map
-// Generation", Fig. 1) computed on bit planes.
-//
-// One layer of the paper maps A_{l-1} to ReLU(maxpool3x3(A_{l-1}) + I_e + I_s).
-// Only whether a cell is positive matters for its first-activation layer, and
-// the positive set of A_l is the 3x3 dilation of the positive set of A_{l-1},
-// intersected with the free cells (an obstacle's -maxint keeps it at zero;
-// a source stays positive). So a layer is, on a 1-bit-per-cell plane,
-//     reached_l = reached_{l-1} | (dilate3x3(reached_{l-1}) & free),
-// and the cells new at layer l get distance l. A 32-bit word holds 32 cells of
-// a row, so one layer is a handful of funnel shifts and three-input logic ops
-// per word instead of nine max operations per cell.
+// Activity propagation for one grid: the stack of max-pool layers (Methods,
+// "Activity Map Generation", Fig. 1) on bit planes (see wave.cuh for why a
+// layer is a 1-bit dilation).
 //
 // k_propagate is persistent and temporally blocked: the grid is cut into tiles;
 // a tile visit loads the tile plus a halo of k rows and one word (32 cells) on
@@ -18,109 +9,21 @@
 // sweep only tiles that the frontier can reach within k layers are visited:
 // a visit that ends with frontier cells queues the tiles they can reach for
 // the next sweep, and blocks claim work from that list.
-// Halo cells are read as of the start of the sweep: a neighbour tile already
-// advanced in this sweep has also published which of its cells it reached in
-// this sweep (nb plane of the sweep's parity), and those bits are masked out.
 //
-// k_plain_layer is the paper's recursive mode, one launch per layer over the
-// whole distance plane, kept as the baseline.
+// k_plain_layer is the paper's recursive mode (Appendix, Table I), one launch
+// per layer over the whole distance plane, kept as the baseline.
 #include <cuda_runtime.h>
 
 #include "mpn_internal.cuh"
+#include "wave.cuh"
 
 namespace mpn {
 
 namespace {
 
-__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Grid-wide barrier for a co-resident (cooperative) grid. The wait is bounded:
-// past spin_limit polls the block records ERR_TIMEOUT and returns false; a
-// block that sees ERR_TIMEOUT already recorded also stops waiting, so one
-// expired wait ends every block instead of starting a new wait in each.
-__device__ bool grid_barrier(Ctl *c, unsigned nblocks, unsigned spin_limit) {
-    __shared__ unsigned s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned ok = 1;
-        const unsigned gen = ld_acquire(&c->bar_gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            unsigned spins = 0;
-            while (ld_acquire(&c->bar_gen) == gen) {
-                if (ld_acquire(&c->err) & ERR_TIMEOUT) {   // another block gave up
-                    ok = 0;
-                    break;
-                }
-                if (++spins > spin_limit) {
-                    atomicOr(&c->err, ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// 3x3 dilation along the row: v | v shifted one cell left | one cell right,
-// with the carries from the neighbouring words of the same row (the lanes of
-// one row group hold consecutive words). At the region's outer words the
-// shuffle returns the lane's own word, so the outermost cell of the region can
-// pick up a wrong bit; that error moves one cell per layer and, with a one-word
-// (32-cell) horizontal halo and at most 32 layers per visit, never reaches the
-// interior.
-template <int RXW>
-__device__ __forceinline__ uint32_t hdil(uint32_t v) {
-    const uint32_t left = __shfl_up_sync(0xffffffffu, v, 1, RXW);
-    const uint32_t right = __shfl_down_sync(0xffffffffu, v, 1, RXW);
-    return v | __funnelshift_l(left, v, 1) | __funnelshift_r(v, right, 1);
-}
-
-// Which border zones of the tile interior a set of frontier cells touches.
-// ri: interior row, wi: interior word, bits: frontier cells of that word.
-__device__ __forceinline__ uint32_t border_bits(int ri, int wi, uint32_t bits, int k, int TY,
-                                                int TXW) {
-    if (!bits) return 0u;
-    const uint32_t lowk = (k >= 32) ? 0xffffffffu : ((1u << k) - 1u);
-    const uint32_t highk = (k >= 32) ? 0xffffffffu : ~((1u << (32 - k)) - 1u);
-    const bool top = ri < k, bot = ri >= TY - k;
-    const bool left = (wi == 0) && (bits & lowk);
-    const bool right = (wi == TXW - 1) && (bits & highk);
-    uint32_t m = FB_ANY;
-    if (top) m |= FB_N;
-    if (bot) m |= FB_S;
-    if (left) m |= FB_W;
-    if (right) m |= FB_E;
-    if (top && left) m |= FB_NW;
-    if (top && right) m |= FB_NE;
-    if (bot && left) m |= FB_SW;
-    if (bot && right) m |= FB_SE;
-    return m;
-}
+using wave::ld_acquire;
+using wave::ld_relaxed;
+using wave::border_bits;
 
 // Queue tile (ty, tx) for sweep s unless it is queued already (one entry per
 // tile per sweep: the stamp only grows).
@@ -148,31 +51,17 @@ __device__ void push_reached(const PropParams &p, int ty, int tx, uint32_t zones
     if (zones & FB_SE) push_tile(p, ty + 1, tx + 1, s);
 }
 
-// Persistent temporally blocked propagation. Block = NW warps; a row group is
-// RXW consecutive lanes holding RXW consecutive words of R consecutive rows
-// (one word per lane per row, in registers). Region = (NW * 32 / RXW * R) rows
-// x RXW words; interior = rows [k, RY - k) x words [1, RXW - 1).
+// Persistent temporally blocked propagation over one grid (tile shapes: see
+// wave::visit_tile).
 template <int RXW, int R, int NW, int MINB, typename DT>
 __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     static_assert(RXW == 4 || RXW == 8 || RXW == 16 || RXW == 32, "row group width");
     static_assert(R >= 2, "rows per lane");
-    constexpr int GPW = 32 / RXW;
-    constexpr int G = NW * GPW;
-
-    __shared__ uint32_t xtop[2][G][RXW];
-    __shared__ uint32_t xbot[2][G][RXW];
+    __shared__ wave::VisitSmem<RXW, NW> sm;
     __shared__ int s_tile;
-    __shared__ unsigned s_mask[2], s_done, s_maxl;   // s_mask by visit parity
+    __shared__ unsigned s_mask[2], s_done, s_maxl, s_ok;   // s_mask by visit parity
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = lane % RXW;
-    const int g = warp * GPW + lane / RXW;
-    const int r0 = g * R;
-    const int k = p.k, TY = p.TY, TXW = p.TXW;
     const int ntiles = p.ntx * p.nty;
-    const GridDev &gd = p.g;
-    DT *dist = reinterpret_cast<DT *>(gd.dist);
-    const bool ownW = (w >= 1) && (w <= TXW);
     Ctl *ctl = p.ctl;
     unsigned thr_maxl = 0u;              // largest layer this thread's words reached
     unsigned long long blk_visits = 0;   // thread 0: tile visits of this block
@@ -182,17 +71,24 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     // bits, so every block takes the same branch)
     if (ld_acquire(&ctl->err) & (ERR_INVAL | ERR_OBSTACLE)) return;
 
+    wave::Visit v;
+    v.g = p.g;
+    v.dist_bits = sizeof(DT) * 8;
+    v.TY = p.TY;
+    v.TXW = p.TXW;
+    v.k = p.k;
     const size_t ntl = (size_t)ntiles;
     for (uint32_t s = 0;; ++s) {
-        const uint32_t l0 = s * (uint32_t)k;
+        const uint32_t l0 = s * (uint32_t)p.k;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             // slot (s + 2) % 3 last served sweep s - 1 and next serves s + 2
             ctl->work[(s + 2) % 3] = 0u;
             ctl->list_len[(s + 2) % 3] = 0u;
         }
-        int jmax = k;
-        if (p.max_layers && l0 + (uint32_t)k > p.max_layers) jmax = (int)(p.max_layers - l0);
-        uint32_t *nbS = (s & 1) ? gd.nb1 : gd.nb0;
+        v.l0 = l0;
+        v.jmax = p.k;
+        if (p.max_layers && l0 + (uint32_t)p.k > p.max_layers) v.jmax = (int)(p.max_layers - l0);
+        v.nbS = (s & 1) ? p.g.nb1 : p.g.nb0;
         const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
         unsigned *work = &ctl->work[s % 3];
         const uint32_t len = ld_acquire(&ctl->list_len[s % 3]);
@@ -211,146 +107,32 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                 next_i = atomicAdd(work, 1u);
                 s_mask[vq] = 0u;   // last read two visits ago, before the previous visit's first barrier
             }
-
-            // ---- load the region (tile + halo) ----
-            const int ty = t / p.ntx, tx = t - ty * p.ntx;
-            const int y0 = ty * TY - k;
-            const int gw = tx * TXW - 1 + w;
-            const bool inX = (gw >= 0) && (gw < gd.P);
-            uint32_t V[R], F[R], NB[R], OWN[R];   // OWN: all-ones on this tile's interior words
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const int rr = r0 + i, y = y0 + rr;
-                const bool in = inX && y >= 0 && y < gd.H;
-                const bool own = ownW && rr >= k && rr < k + TY;
-                const size_t off = (size_t)y * gd.P + gw;
-                OWN[i] = own ? 0xffffffffu : 0u;
-                F[i] = in ? __ldg(gd.free_bits + off) : 0u;
-                V[i] = in ? ld_relaxed(gd.vis + off) : 0u;
-                NB[i] = 0u;
-            }
-            __threadfence();   // visit bits before the matching this-sweep bits
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-                if (!OWN[i] && V[i]) V[i] &= ~ld_relaxed(nbS + (size_t)(y0 + r0 + i) * gd.P + gw);
-
-            // ---- up to k layers in registers ----
-            // P[b][i]: bit b of (layer - l0 - 1) for cells first reached in
-            // this visit, so each cell's distance is written once, at the end.
-            uint32_t P[5][R];
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-#pragma unroll
-                for (int b = 0; b < 5; ++b) P[b][i] = 0u;
-            }
-            uint32_t changed = 1u;
-            unsigned lastj = 0u;
-            for (int j = 1; j <= jmax; ++j) {
-                const uint32_t hF = hdil<RXW>(V[0]);
-                const uint32_t hL = hdil<RXW>(V[R - 1]);
-                xtop[j & 1][g][w] = hF;
-                xbot[j & 1][g][w] = hL;
-                if (!__syncthreads_or(changed != 0u)) break;   // region is stable
-                const uint32_t hUp = (g > 0) ? xbot[j & 1][g - 1][w] : 0u;
-                const uint32_t hDn = (g < G - 1) ? xtop[j & 1][g + 1][w] : 0u;
-                uint32_t h[R];
-                h[0] = hF;
-                h[R - 1] = hL;
-#pragma unroll
-                for (int i = 1; i < R - 1; ++i) h[i] = hdil<RXW>(V[i]);
-                uint32_t M[5];   // all-ones where bit b of j - 1 is set (block-uniform)
-#pragma unroll
-                for (int b = 0; b < 5; ++b) M[b] = (((j - 1) >> b) & 1) ? 0xffffffffu : 0u;
-                changed = 0u;
-                uint32_t own_new = 0u;
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const uint32_t up = (i > 0) ? h[i - 1] : hUp;
-                    const uint32_t dn = (i < R - 1) ? h[i + 1] : hDn;
-                    const uint32_t nv = (up | h[i] | dn) & F[i] & ~V[i];
-                    V[i] |= nv;
-                    changed |= nv;
-                    const uint32_t onv = nv & OWN[i];
-                    NB[i] |= onv;
-                    own_new |= onv;
-#pragma unroll
-                    for (int b = 0; b < 5; ++b) P[b][i] |= onv & M[b];
-                }
-                if (own_new) lastj = (unsigned)j;
-            }
-
-            // the claimed index has arrived by now; fetch its tile id early
-            int next_t = -1;
-            if (threadIdx.x == 0 && next_i < len) next_t = (int)ld_relaxed(list + next_i);
-
-            // ---- frontier zones: cells reached at layer l0 + k ----
-            uint32_t fmask = 0u;
-            if (jmax == k) {
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    uint32_t last = NB[i];
-#pragma unroll
-                    for (int b = 0; b < 5; ++b)
-                        last &= (((k - 1) >> b) & 1) ? P[b][i] : ~P[b][i];
-                    fmask |= border_bits(r0 + i - k, w - 1, last, k, TY, TXW);
-                }
-            }
+            v.ty = t / p.ntx;
+            v.tx = t - v.ty * p.ntx;
+            uint32_t fmask;
+            unsigned lastj;
+            wave::visit_tile<RXW, R, NW>(v, sm, &ctl->err, &fmask, &lastj);
             if (fmask) atomicOr(&s_mask[vq], fmask);
             if (lastj) thr_maxl = max(thr_maxl, l0 + lastj);
-
-            // ---- distances of the cells first reached in this visit ----
-            // The warp writes one changed word at a time: 32 lanes, 32
-            // consecutive cells, one coalesced store.
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                unsigned act = __ballot_sync(0xffffffffu, NB[i] != 0u);
-                while (act) {
-                    const int src = __ffs(act) - 1;
-                    act &= act - 1u;
-                    const uint32_t nb = __shfl_sync(0xffffffffu, NB[i], src);
-                    uint32_t off = 0u;
-#pragma unroll
-                    for (int b = 0; b < 5; ++b)
-                        off |= ((__shfl_sync(0xffffffffu, P[b][i], src) >> lane) & 1u) << b;
-                    const int sw = src % RXW;                         // source word column
-                    const int sg = warp * GPW + src / RXW;            // source row group
-                    const int y = y0 + sg * R + i;
-                    const int gws = tx * TXW - 1 + sw;
-                    if ((nb >> lane) & 1u) {
-                        const uint32_t layer = l0 + 1u + off;
-                        if (sizeof(DT) == 2 && layer > 0xfffeu) atomicOr(&ctl->err, ERR_OVERFLOW);
-                        else dist[(size_t)y * gd.W + (size_t)gws * 32 + lane] = (DT)layer;
-                    }
-                }
-            }
-
-            // ---- publish: this-sweep bits, then visit bits, then the queue ----
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-                if (NB[i]) st_relaxed(nbS + (size_t)(y0 + r0 + i) * gd.P + gw, NB[i]);
-            __threadfence();
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-                if (NB[i]) st_relaxed(gd.vis + (size_t)(y0 + r0 + i) * gd.P + gw, V[i]);
             if (threadIdx.x == 0) {
                 ++blk_visits;
-                s_tile = next_t;
+                s_tile = (next_i < len) ? (int)ld_relaxed(list + next_i) : -1;
             }
             __syncthreads();
             if (threadIdx.x < 9) {
                 // lanes 0..8 each queue one of the tiles the frontier reaches
                 const uint32_t zone = 1u << threadIdx.x;
-                if (s_mask[vq] & zone) push_reached(p, ty, tx, zone, s + 1);
+                if (s_mask[vq] & zone) push_reached(p, v.ty, v.tx, zone, s + 1);
             }
             t = s_tile;
         }
 
-        if (!grid_barrier(ctl, gridDim.x, p.spin_limit)) return;
+        if (!wave::grid_barrier(ctl, gridDim.x, p.spin_limit, &s_ok)) return;
         if (threadIdx.x == 0) {
             // decided from values no block changes before the next barrier, so
             // every block reaches the same decision
             unsigned done = (ld_acquire(&ctl->list_len[(s + 1) % 3]) == 0u) ||
-                            (p.max_layers && l0 + (uint32_t)k >= p.max_layers);
+                            (p.max_layers && l0 + (uint32_t)p.k >= p.max_layers);
             if (!done && s + 1 >= p.sweep_cap) {
                 atomicOr(&ctl->err, ERR_SWEEPS);
                 done = 1;

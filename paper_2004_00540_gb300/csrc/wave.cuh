@@ -1,0 +1,279 @@
+// Device code shared by the single-grid and the batched propagation kernels:
+// memory-order helpers, the bounded grid barrier, and one tile visit (k layers
+// of the max-pool wave on bit planes in registers).
+//
+// One layer of the paper maps A_{l-1} to ReLU(maxpool3x3(A_{l-1}) + I_e + I_s)
+// (Methods, "Activity Map Generation"). Only whether a cell is positive
+// matters for its first-activation layer, and the positive set of A_l is the
+// 3x3 dilation of the positive set of A_{l-1} intersected with the free cells
+// (an obstacle's -maxint keeps it at zero; a source stays positive). So on a
+// 1-bit-per-cell plane a layer is
+//     reached_l = reached_{l-1} | (dilate3x3(reached_{l-1}) & free),
+// and the cells new at layer l get distance l. A 32-bit word holds 32 cells of
+// a row: one layer costs a few funnel shifts and three-input logic operations
+// per word instead of nine max operations per cell.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mpn_internal.cuh"
+
+namespace mpn {
+namespace wave {
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a co-resident (cooperative) grid. The wait is bounded:
+// past spin_limit polls the block records ERR_TIMEOUT and returns false; a
+// block that sees ERR_TIMEOUT already recorded also stops waiting, so one
+// expired wait ends every block instead of starting a new wait in each.
+__device__ __forceinline__ bool grid_barrier(Ctl *c, unsigned nblocks, unsigned spin_limit,
+                                             unsigned *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned ok = 1;
+        const unsigned gen = ld_acquire(&c->bar_gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            unsigned spins = 0;
+            while (ld_acquire(&c->bar_gen) == gen) {
+                if (ld_acquire(&c->err) & ERR_TIMEOUT) {   // another block gave up
+                    ok = 0;
+                    break;
+                }
+                if (++spins > spin_limit) {
+                    atomicOr(&c->err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// 3x3 dilation along the row: v | v shifted one cell left | one cell right,
+// with the carries from the neighbouring words of the same row (the lanes of
+// one row group hold consecutive words). At the region's outer words the
+// shuffle returns the lane's own word, so the outermost cell of the region can
+// pick up a wrong bit; that error moves one cell per layer and, with a one-word
+// (32-cell) horizontal halo and at most 32 layers per visit, never reaches the
+// interior.
+template <int RXW>
+__device__ __forceinline__ uint32_t hdil(uint32_t v) {
+    const uint32_t left = __shfl_up_sync(0xffffffffu, v, 1, RXW);
+    const uint32_t right = __shfl_down_sync(0xffffffffu, v, 1, RXW);
+    return v | __funnelshift_l(left, v, 1) | __funnelshift_r(v, right, 1);
+}
+
+// Which border zones of the tile interior a set of frontier cells touches.
+// ri: interior row, wi: interior word, bits: frontier cells of that word.
+__device__ __forceinline__ uint32_t border_bits(int ri, int wi, uint32_t bits, int k, int TY,
+                                                int TXW) {
+    if (!bits) return 0u;
+    const uint32_t lowk = (k >= 32) ? 0xffffffffu : ((1u << k) - 1u);
+    const uint32_t highk = (k >= 32) ? 0xffffffffu : ~((1u << (32 - k)) - 1u);
+    const bool top = ri < k, bot = ri >= TY - k;
+    const bool left = (wi == 0) && (bits & lowk);
+    const bool right = (wi == TXW - 1) && (bits & highk);
+    uint32_t m = FB_ANY;
+    if (top) m |= FB_N;
+    if (bot) m |= FB_S;
+    if (left) m |= FB_W;
+    if (right) m |= FB_E;
+    if (top && left) m |= FB_NW;
+    if (top && right) m |= FB_NE;
+    if (bot && left) m |= FB_SW;
+    if (bot && right) m |= FB_SE;
+    return m;
+}
+
+// One tile visit's inputs.
+struct Visit {
+    GridDev g;            // planes of the grid the tile belongs to
+    uint32_t *nbS;        // this-sweep plane of the sweep's parity
+    int dist_bits;        // 16 or 32
+    int TY, TXW, k;       // tile geometry and depth
+    int ty, tx;           // tile coordinates within its grid
+    uint32_t l0;          // layer at the start of the sweep
+    int jmax;             // layers to run (k, or fewer at a layer cap)
+};
+
+template <int RXW, int NW>
+struct VisitSmem {
+    static constexpr int G = NW * (32 / RXW);
+    uint32_t xtop[2][G][RXW];
+    uint32_t xbot[2][G][RXW];
+};
+
+// Advance one tile by up to v.jmax layers, write the distances of the cells it
+// reaches (a uint16 overflow sets ERR_OVERFLOW in *err), publish its new visit
+// bits (after the this-sweep bits) and return
+// the border zones of its frontier (cells reached at layer l0 + k) and, per
+// thread, the last layer at which one of this thread's cells was reached.
+// Every thread of the block calls it; it contains block barriers.
+//
+// Block layout: a row group is RXW consecutive lanes holding RXW consecutive
+// words of R consecutive rows (one word per lane per row, in registers).
+// Region = (NW * 32 / RXW * R) rows x RXW words; interior = rows [k, RY - k)
+// x words [1, RXW - 1). Halo words of other tiles are read as of the start of
+// the sweep: their this-sweep bits are masked out (the owner writes those
+// before its visit bits; the fences order both sides).
+template <int RXW, int R, int NW>
+__device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
+                                           uint32_t *fmask_out, unsigned *lastj_out) {
+    constexpr int GPW = 32 / RXW;
+    constexpr int G = NW * GPW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = lane % RXW;
+    const int g = warp * GPW + lane / RXW;
+    const int r0 = g * R;
+    const int k = v.k, TY = v.TY, TXW = v.TXW;
+    const GridDev &gd = v.g;
+    const bool ownW = (w >= 1) && (w <= TXW);
+
+    // ---- load the region (tile + halo) ----
+    const int y0 = v.ty * TY - k;
+    const int gw = v.tx * TXW - 1 + w;
+    const bool inX = (gw >= 0) && (gw < gd.P);
+    uint32_t V[R], F[R], NB[R], OWN[R];   // OWN: all-ones on this tile's interior words
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int rr = r0 + i, y = y0 + rr;
+        const bool in = inX && y >= 0 && y < gd.H;
+        const bool own = ownW && rr >= k && rr < k + TY;
+        const size_t off = (size_t)y * gd.P + gw;
+        OWN[i] = own ? 0xffffffffu : 0u;
+        F[i] = in ? __ldg(gd.free_bits + off) : 0u;
+        V[i] = in ? ld_relaxed(gd.vis + off) : 0u;
+        NB[i] = 0u;
+    }
+    __threadfence();   // visit bits before the matching this-sweep bits
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (!OWN[i] && V[i]) V[i] &= ~ld_relaxed(v.nbS + (size_t)(y0 + r0 + i) * gd.P + gw);
+
+    // ---- up to k layers in registers ----
+    // P[b][i]: bit b of (layer - l0 - 1) for cells first reached in this
+    // visit, so each cell's distance is written once, at the end.
+    uint32_t P[5][R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+#pragma unroll
+        for (int b = 0; b < 5; ++b) P[b][i] = 0u;
+    }
+    uint32_t changed = 1u;
+    unsigned lastj = 0u;
+    for (int j = 1; j <= v.jmax; ++j) {
+        const uint32_t hF = hdil<RXW>(V[0]);
+        const uint32_t hL = hdil<RXW>(V[R - 1]);
+        sm.xtop[j & 1][g][w] = hF;
+        sm.xbot[j & 1][g][w] = hL;
+        if (!__syncthreads_or(changed != 0u)) break;   // region is stable
+        const uint32_t hUp = (g > 0) ? sm.xbot[j & 1][g - 1][w] : 0u;
+        const uint32_t hDn = (g < G - 1) ? sm.xtop[j & 1][g + 1][w] : 0u;
+        uint32_t h[R];
+        h[0] = hF;
+        h[R - 1] = hL;
+#pragma unroll
+        for (int i = 1; i < R - 1; ++i) h[i] = hdil<RXW>(V[i]);
+        uint32_t M[5];   // all-ones where bit b of j - 1 is set (block-uniform)
+#pragma unroll
+        for (int b = 0; b < 5; ++b) M[b] = (((j - 1) >> b) & 1) ? 0xffffffffu : 0u;
+        changed = 0u;
+        uint32_t own_new = 0u;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const uint32_t up = (i > 0) ? h[i - 1] : hUp;
+            const uint32_t dn = (i < R - 1) ? h[i + 1] : hDn;
+            const uint32_t nv = (up | h[i] | dn) & F[i] & ~V[i];
+            V[i] |= nv;
+            changed |= nv;
+            const uint32_t onv = nv & OWN[i];
+            NB[i] |= onv;
+            own_new |= onv;
+#pragma unroll
+            for (int b = 0; b < 5; ++b) P[b][i] |= onv & M[b];
+        }
+        if (own_new) lastj = (unsigned)j;
+    }
+
+    // ---- frontier zones: cells reached at layer l0 + k ----
+    uint32_t fmask = 0u;
+    if (v.jmax == k) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            uint32_t last = NB[i];
+#pragma unroll
+            for (int b = 0; b < 5; ++b) last &= (((k - 1) >> b) & 1) ? P[b][i] : ~P[b][i];
+            fmask |= border_bits(r0 + i - k, w - 1, last, k, TY, TXW);
+        }
+    }
+    *fmask_out = fmask;
+    *lastj_out = lastj;
+
+    // ---- distances of the cells first reached in this visit ----
+    // The warp writes one changed word at a time: 32 lanes, 32 consecutive
+    // cells, one coalesced store.
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        unsigned act = __ballot_sync(0xffffffffu, NB[i] != 0u);
+        while (act) {
+            const int src = __ffs(act) - 1;
+            act &= act - 1u;
+            const uint32_t nb = __shfl_sync(0xffffffffu, NB[i], src);
+            uint32_t off = 0u;
+#pragma unroll
+            for (int b = 0; b < 5; ++b)
+                off |= ((__shfl_sync(0xffffffffu, P[b][i], src) >> lane) & 1u) << b;
+            const int sw = src % RXW;                 // source word column
+            const int sg = warp * GPW + src / RXW;    // source row group
+            const int y = y0 + sg * R + i;
+            const size_t cell = (size_t)y * gd.W + (size_t)(v.tx * TXW - 1 + sw) * 32 + lane;
+            if ((nb >> lane) & 1u) {
+                const uint32_t layer = v.l0 + 1u + off;
+                if (v.dist_bits == 16) {
+                    if (layer > 0xfffeu) atomicOr(err, ERR_OVERFLOW);
+                    else reinterpret_cast<uint16_t *>(gd.dist)[cell] = (uint16_t)layer;
+                } else {
+                    reinterpret_cast<uint32_t *>(gd.dist)[cell] = layer;
+                }
+            }
+        }
+    }
+
+    // ---- publish: this-sweep bits, then visit bits ----
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (NB[i]) st_relaxed(v.nbS + (size_t)(y0 + r0 + i) * gd.P + gw, NB[i]);
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (NB[i]) st_relaxed(gd.vis + (size_t)(y0 + r0 + i) * gd.P + gw, V[i]);
+}
+
+}  // namespace wave
+}  // namespace mpn

@@ -28,7 +28,11 @@ EXPORTS = (
     "mpn_propagate_plain", "mpn_get_distances", "mpn_get_activity", "mpn_trace_lengths",
     "mpn_trace", "mpn_sync", "mpn_destroy", "mpn_status_str", "mpn_set_tuning",
     "mpn_variant_info", "mpn_get_stats", "mpn_launch_count", "mpn_propagate_noalloc",
+    "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_submit", "mpn_batch_run",
+    "mpn_batch_poll", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
+    "mpn_batch_stats", "mpn_batch_destroy",
 )
+MPN_BATCH_PENDING, MPN_BATCH_DONE, MPN_BATCH_FAILED = 0, 1, 2
 
 
 class MPNError(RuntimeError):
@@ -44,6 +48,20 @@ class mpn_stats(ctypes.Structure):
         ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("blocks", ctypes.c_int32),
         ("layers", ctypes.c_uint32), ("sweeps", ctypes.c_uint32), ("tile_visits", ctypes.c_uint64),
         ("ms_encode", ctypes.c_float), ("ms_propagate", ctypes.c_float), ("ms_trace", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class mpn_batch_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("arena_bytes", ctypes.c_uint64), ("arena_used", ctypes.c_uint64),
+        ("tiles_used", ctypes.c_uint64), ("next_sweep", ctypes.c_uint32),
+        ("rounds", ctypes.c_uint64), ("sweeps", ctypes.c_uint64),
+        ("last_round_ms", ctypes.c_float), ("blocks", ctypes.c_int32),
+        ("admitted", ctypes.c_int32), ("running", ctypes.c_int32), ("done", ctypes.c_int32),
+        ("failed", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -88,6 +106,18 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
             "mpn_get_stats": ([vp, ctypes.POINTER(mpn_stats)], ctypes.c_int),
             "mpn_launch_count": ([], u64),
             "mpn_propagate_noalloc": ([vp, i32, i32, vp, i32, u32, vp, vp], ctypes.c_int),
+            "mpn_batch_create": ([u64, i32, vp, pp], ctypes.c_int),
+            "mpn_batch_set_depth": ([vp, i32], ctypes.c_int),
+            "mpn_batch_submit": ([vp, vp, i32, i32, vp, i32, vp, i32, i32, u32,
+                                  ctypes.POINTER(u64)], ctypes.c_int),
+            "mpn_batch_run": ([vp, u32, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
+            "mpn_batch_poll": ([vp, u64, ctypes.POINTER(i32)], ctypes.c_int),
+            "mpn_batch_result": ([vp, u64, vp, vp, vp, u64, vp, ctypes.POINTER(u32)], ctypes.c_int),
+            "mpn_batch_info": ([vp, u64, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                ctypes.POINTER(i32), ctypes.POINTER(u64)], ctypes.c_int),
+            "mpn_batch_release": ([vp, u64], ctypes.c_int),
+            "mpn_batch_stats": ([vp, ctypes.POINTER(mpn_batch_stats_t)], ctypes.c_int),
+            "mpn_batch_destroy": ([vp], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -327,3 +357,99 @@ class Planner:
 
     def stats(self) -> dict:
         return mpn_get_stats(self.ctx)
+
+
+# ---- batched / continuously batched solving ------------------------------
+
+class Batch:
+    """Many grids on one GPU: admission by device memory, rounds of one
+    persistent launch over every admitted grid (see include/mpn.h)."""
+
+    def __init__(self, budget_bytes: int, variant: int = -1, stream=None):
+        self.h = ctypes.c_void_p()
+        _check(load().mpn_batch_create(budget_bytes, variant, _stream_handle(stream),
+                                       ctypes.byref(self.h)), "mpn_batch_create")
+
+    def close(self):
+        if self.h:
+            load().mpn_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_depth(self, depth: int):
+        _check(load().mpn_batch_set_depth(self.h, depth), "mpn_batch_set_depth")
+
+    def submit(self, mask, targets, starts, dist_bits: int = MPN_DIST_AUTO, max_layers: int = 0):
+        """Ticket, or None when the grid does not fit in the arena now."""
+        H, W = int(mask.shape[0]), int(mask.shape[1])
+        t = targets if hasattr(targets, "data_ptr") else np.ascontiguousarray(targets, np.uint32)
+        s = starts if hasattr(starts, "data_ptr") else np.ascontiguousarray(starts, np.uint32)
+        nt = int(t.numel() if hasattr(t, "numel") else t.size)
+        ns = int(s.numel() if hasattr(s, "numel") else s.size)
+        tk = ctypes.c_uint64(0)
+        st = load().mpn_batch_submit(self.h, _ptr(mask)[0], H, W, _ptr(t)[0], nt, _ptr(s)[0], ns,
+                                     dist_bits, max_layers, ctypes.byref(tk))
+        if st == MPN_ENOMEM:
+            return None
+        _check(st, "mpn_batch_submit")
+        return int(tk.value)
+
+    def run(self, max_sweeps: int = 0):
+        """One round; returns (grids still in flight, grids finished)."""
+        r, d = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().mpn_batch_run(self.h, max_sweeps, ctypes.byref(r), ctypes.byref(d)),
+               "mpn_batch_run")
+        return r.value, d.value
+
+    def poll(self, ticket: int) -> int:
+        s = ctypes.c_int32(0)
+        st = load().mpn_batch_poll(self.h, ticket, ctypes.byref(s))
+        if s.value == MPN_BATCH_FAILED:
+            return MPN_BATCH_FAILED
+        _check(st, "mpn_batch_poll")
+        return s.value
+
+    def error(self, ticket: int) -> int:
+        s = ctypes.c_int32(0)
+        return int(load().mpn_batch_poll(self.h, ticket, ctypes.byref(s)))
+
+    def info(self, ticket: int) -> dict:
+        H, W, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        tot = ctypes.c_uint64()
+        _check(load().mpn_batch_info(self.h, ticket, ctypes.byref(H), ctypes.byref(W),
+                                     ctypes.byref(b), ctypes.byref(tot)), "mpn_batch_info")
+        return {"H": H.value, "W": W.value, "dist_bits": b.value, "total_cells": tot.value}
+
+    def result(self, ticket: int, n_starts: int, want_dist: bool = True):
+        """(dist or None, Paths, layers) of a finished grid, on the host."""
+        inf = self.info(ticket)
+        dist = None
+        if want_dist:
+            dist = np.empty((inf["H"], inf["W"]), np.uint16 if inf["dist_bits"] == 16 else np.uint32)
+        off = np.zeros(n_starts + 1, np.uint64)
+        cells = np.zeros(max(inf["total_cells"], 1), np.uint32)
+        status = np.zeros(max(n_starts, 1), np.int8)
+        layers = ctypes.c_uint32(0)
+        _check(load().mpn_batch_result(self.h, ticket, _ptr(dist)[0] if dist is not None else None,
+                                       _ptr(off)[0], _ptr(cells)[0], cells.size, _ptr(status)[0],
+                                       ctypes.byref(layers)), "mpn_batch_result")
+        return dist, Paths(off, cells[:inf["total_cells"]], status[:n_starts]), int(layers.value)
+
+    def release(self, ticket: int):
+        _check(load().mpn_batch_release(self.h, ticket), "mpn_batch_release")
+
+    def stats(self) -> dict:
+        s = mpn_batch_stats_t()
+        _check(load().mpn_batch_stats(self.h, ctypes.byref(s)), "mpn_batch_stats")
+        return s.as_dict()

@@ -1,0 +1,100 @@
+"""Continuous-batching request loop over the batched engine (include/mpn.h,
+mpn_batch_*).
+
+Requests (a grid, its targets and starts) arrive over time. The loop admits
+waiting requests in arrival order while the batch's device arena has room
+(admission by device memory), runs one round -- one persistent launch that
+advances every admitted grid for a bounded number of sweeps -- collects the
+grids that finished (their paths are downloaded as the response) and
+releases them, so that arrivals during a round join at the next one. All
+GPU work runs in the library; this module only schedules and keeps time.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .mpn import Batch, MPN_BATCH_DONE, MPN_BATCH_PENDING
+
+
+@dataclass
+class Request:
+    mask: np.ndarray
+    targets: np.ndarray
+    starts: np.ndarray
+    dist_bits: int = 0
+    arrival: float = 0.0          # seconds after the start of the run
+
+
+@dataclass
+class ServeReport:
+    latencies: list = field(default_factory=list)   # seconds, per request, arrival -> response
+    makespan: float = 0.0
+    rounds: int = 0
+    refused_admissions: int = 0                      # submit attempts that did not fit yet
+    results: dict = field(default_factory=dict)      # request index -> Paths (if kept)
+    failed: list = field(default_factory=list)
+
+    def summary(self) -> dict:
+        lat = np.asarray(self.latencies) * 1e3
+        n = len(self.latencies)
+        return {
+            "requests": n,
+            "makespan_s": self.makespan,
+            "mazes_per_s": n / self.makespan if self.makespan > 0 else None,
+            "p50_ms": float(np.percentile(lat, 50)) if n else None,
+            "p99_ms": float(np.percentile(lat, 99)) if n else None,
+            "mean_ms": float(lat.mean()) if n else None,
+            "rounds": self.rounds,
+            "refused_admissions": self.refused_admissions,
+            "failed": len(self.failed),
+        }
+
+
+def serve(batch: Batch, requests: list, round_sweeps: int = 64, keep_results: bool = False,
+          clock=time.perf_counter) -> ServeReport:
+    """Run every request through the batch as it arrives; returns latencies."""
+    rep = ServeReport()
+    order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
+    waiting = collections.deque()
+    in_flight = {}                 # ticket -> request index
+    nxt = 0
+    t0 = clock()
+    while nxt < len(order) or waiting or in_flight:
+        now = clock() - t0
+        while nxt < len(order) and requests[order[nxt]].arrival <= now:
+            waiting.append(order[nxt])
+            nxt += 1
+        while waiting:
+            r = requests[waiting[0]]
+            tk = batch.submit(r.mask, r.targets, r.starts, r.dist_bits)
+            if tk is None:
+                rep.refused_admissions += 1
+                break
+            in_flight[tk] = waiting.popleft()
+        if in_flight:
+            batch.run(round_sweeps)
+            rep.rounds += 1
+            for tk in list(in_flight):
+                st = batch.poll(tk)
+                if st == MPN_BATCH_PENDING:
+                    continue
+                i = in_flight.pop(tk)
+                if st == MPN_BATCH_DONE:
+                    _, paths, _ = batch.result(tk, requests[i].starts.size, want_dist=False)
+                    if keep_results:
+                        rep.results[i] = paths
+                else:
+                    rep.failed.append(i)
+                batch.release(tk)
+                rep.latencies.append(clock() - t0 - requests[i].arrival)
+        elif nxt < len(order):
+            wait = requests[order[nxt]].arrival - (clock() - t0)
+            if wait > 0:
+                time.sleep(min(wait, 0.05))
+    rep.makespan = clock() - t0
+    return rep
+

@@ -1,0 +1,125 @@
+"""Batched and continuously batched solving: every grid's distances and paths
+are the same bit for bit as the oracle's (and so as the grid solved alone),
+whatever else is in the batch, in whatever order and round it arrives."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_2004_00540_gb300 as pkg
+from gpu_util import widen
+
+pytestmark = pytest.mark.gpu
+
+
+def small_members(n, side_hi=300, base_seed=4):
+    return [synth.c4_member(i, base_seed, 64, side_hi) for i in range(n)]
+
+
+def check(b, tk, w):
+    dist, paths, layers = b.result(tk, w.starts.size)
+    od, oL = oracle.bfs(w.mask, w.targets)
+    assert np.array_equal(widen(dist), od), w.name
+    assert layers == oL
+    off, cells, status = oracle.trace(w.mask, od, w.starts)
+    assert np.array_equal(paths.offsets, off)
+    assert np.array_equal(paths.status, status)
+    assert np.array_equal(paths.cells, cells)
+
+
+def test_batch_all_at_once():
+    ws = small_members(24)
+    with pkg.Batch(1 << 30) as b:
+        tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
+        assert all(t is not None for t in tks)
+        running, done = b.run(0)
+        assert running == 0 and done == len(ws)
+        for tk, w in zip(tks, ws):
+            assert b.poll(tk) == pkg.MPN_BATCH_DONE
+            check(b, tk, w)
+            b.release(tk)
+        assert b.stats()["arena_used"] == 0
+
+
+def test_batch_continuous_arrivals_and_short_rounds():
+    ws = small_members(30, side_hi=400, base_seed=40)
+    rng = np.random.default_rng(1)
+    order = rng.permutation(len(ws))
+    with pkg.Batch(1 << 30) as b:
+        b.set_depth(16)
+        tickets = {}
+        pending = list(order)
+        rounds = 0
+        while pending or any(b.poll(t) == pkg.MPN_BATCH_PENDING for t in tickets):
+            for _ in range(int(rng.integers(0, 4))):          # a few arrivals per round
+                if pending:
+                    i = pending.pop()
+                    tickets[b.submit(ws[i].mask, ws[i].targets, ws[i].starts, ws[i].dist_bits)] = i
+            b.run(int(rng.integers(1, 6)))                     # short rounds: grids span rounds
+            rounds += 1
+            assert rounds < 100000
+        for tk, i in tickets.items():
+            check(b, tk, ws[i])
+        assert b.stats()["rounds"] > 3
+
+
+def test_batch_admission_by_memory():
+    ws = small_members(12, side_hi=500, base_seed=90)
+    with pkg.Batch(3 << 20) as b:                               # room for only a few grids
+        admitted, refused = [], []
+        for w in ws:
+            tk = b.submit(w.mask, w.targets, w.starts, w.dist_bits)
+            (admitted if tk is not None else refused).append((tk, w))
+        assert admitted and refused
+        b.run(0)
+        for tk, w in admitted:
+            check(b, tk, w)
+            b.release(tk)
+        # freed memory admits the rest
+        for _, w in refused[:3]:
+            tk = b.submit(w.mask, w.targets, w.starts, w.dist_bits)
+            assert tk is not None
+            b.run(0)
+            check(b, tk, w)
+            b.release(tk)
+
+
+def test_batch_rejects_bad_endpoints_and_overflow_fails_alone():
+    ws = small_members(6, base_seed=7)
+    bad = ws[0]
+    obst = np.flatnonzero(bad.mask.reshape(-1))[:1].astype(np.uint32)
+    with pkg.Batch(1 << 28) as b:
+        with pytest.raises(pkg.MPNError) as e:
+            b.submit(bad.mask, obst, bad.starts, bad.dist_bits)
+        assert e.value.status == pkg.MPN_EOBSTACLE
+        with pytest.raises(pkg.MPNError) as e:
+            b.submit(bad.mask, bad.targets, np.array([bad.H * bad.W], np.uint32), bad.dist_bits)
+        assert e.value.status == pkg.MPN_EINVAL
+        corridor = synth.empty(1, 70000)                  # distances past 65534 in uint16
+        to = b.submit(corridor, np.array([0], np.uint32), np.array([69999], np.uint32), 16)
+        good = [(b.submit(w.mask, w.targets, w.starts, w.dist_bits), w) for w in ws[1:]]
+        while b.stats()["running"] or b.stats()["admitted"]:
+            b.run(0)
+        assert b.poll(to) == pkg.MPN_BATCH_FAILED
+        assert b.error(to) == pkg.MPN_EOVERFLOW
+        for tk, w in good:
+            check(b, tk, w)
+
+
+def test_batch_fixed_depth():
+    w = synth.c4_member(2, 4, 64, 300)
+    with pkg.Batch(1 << 28) as b:
+        tk = b.submit(w.mask, w.targets, w.starts, w.dist_bits, max_layers=9)
+        b.run(0)
+        dist, paths, layers = b.result(tk, w.starts.size)
+    od, oL = oracle.bfs(w.mask, w.targets, max_layers=9)
+    assert np.array_equal(widen(dist), od) and layers == oL
+
+
+def test_batch_full_size_members_sample():
+    ws = [synth.c4_member(i) for i in (0, 1, 2, 3, 101, 254, 255)]
+    with pkg.Batch(16 << 30) as b:
+        tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
+        b.run(0)
+        for tk, w in zip(tks, ws):
+            check(b, tk, w)

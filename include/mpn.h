@@ -158,6 +158,34 @@ mpn_status mpn_trace_lengths(mpn_ctx *ctx, const uint32_t *starts, int32_t n,
 mpn_status mpn_trace(mpn_ctx *ctx, const uint32_t *starts, int32_t n, uint64_t *offsets,
                      uint32_t *cells, uint64_t cells_cap, int8_t *status);
 
+/*
+ * Euclidean path reconstruction (Methods, "Path Reconstruction", Eq. 1 and
+ * the straightening that follows it): from each start, step to the
+ * 4-neighbour (left, right, up, down, in Eq. 1's order) with the largest
+ * activity, i.e. distance d - 1; then drop every point whose neighbours on
+ * the path are sqrt(2) apart. Eq. 1 does not say what happens when no
+ * 4-neighbour is one step closer (the closer cell is diagonal); this build
+ * steps to the first 4-neighbour at the same distance that is 4-adjacent to a
+ * closer cell (the corner of the diagonal move), or, if both corners are
+ * obstacles, takes the diagonal step. Straightening scans forward: P(t) is
+ * dropped when the last kept point and P(t+1) are sqrt(2) apart. Output and
+ * errors as in mpn_trace (offsets[i+1] - offsets[i] = straightened length).
+ */
+mpn_status mpn_trace_euclid(mpn_ctx *ctx, const uint32_t *starts, int32_t n, uint64_t *offsets,
+                            uint32_t *cells, uint64_t cells_cap, int8_t *status);
+
+/*
+ * Nearest target of each start (the paper's multi-source, multi-target use:
+ * each customer's closest taxi, Results, "Multi-source Multi-target Path
+ * Planning"): the target that simple path reconstruction from the start ends
+ * at -- one of the nearest targets, chosen by the lowest-index descent -- and
+ * the start's distance to it, without storing the paths. target[n] and
+ * dist[n] (dist may be NULL), uint32, host or device; 0xFFFFFFFF for a start
+ * that is unreachable or on an obstacle. Errors as in mpn_trace.
+ */
+mpn_status mpn_nearest_targets(mpn_ctx *ctx, const uint32_t *starts, int32_t n,
+                               uint32_t *target, uint32_t *dist);
+
 /* Wait for the context's stream; report any error the GPU recorded. */
 mpn_status mpn_sync(mpn_ctx *ctx);
 
@@ -173,6 +201,18 @@ const char *mpn_status_str(mpn_status s);
  * variant < 0 restores the automatic choice.
  */
 mpn_status mpn_set_tuning(mpn_ctx *ctx, int32_t variant, int32_t depth);
+
+/*
+ * Autotuner: time every compiled tile shape and every depth in {8, 12, 16,
+ * 24, 32} (where the shape allows it) by propagating from these targets on
+ * this context's grid; keep the fastest for the context and record, for the
+ * grid's size bucket ceil(log2(max(H, W))), the fastest depth per shape and
+ * the fastest shape overall. Contexts created later with automatic tiling,
+ * and batches (for their shape), start from the recorded choice. Leaves the
+ * context without distances (propagate again). Outputs may be NULL.
+ */
+mpn_status mpn_autotune(mpn_ctx *ctx, const uint32_t *targets, int32_t n_targets,
+                        int32_t *variant, int32_t *depth, float *best_ms);
 
 /* Shape of compiled tile variant v: region rows, region words (32 cells
  * each), threads per block. MPN_EINVAL past the last variant. */
@@ -195,6 +235,10 @@ mpn_status mpn_get_stats(mpn_ctx *ctx, mpn_stats *out);
 /* Number of kernels this library has launched in this process. */
 uint64_t mpn_launch_count(void);
 
+/* Text of the last CUDA runtime error behind an MPN_ECUDA / MPN_ENOMEM
+ * returned to this host thread ("" if none). */
+const char *mpn_last_error(void);
+
 /* ------------------------------------------------------------------------
  * Batched and continuously batched solving of many grids.
  *
@@ -214,7 +258,10 @@ uint64_t mpn_launch_count(void);
  * buffer, or through a temporary device buffer for a host one -- the one
  * allocation outside the budget.)
  * Grids submitted while others are in flight join at the next round, so
- * their work overlaps on the device. Results are the same as one grid solved
+ * their work overlaps on the device. A round (device-side preparation plus
+ * the cooperative launch) is captured once per max_sweeps value as a CUDA
+ * graph and replayed; its launch parameters never change because the
+ * per-round state lives in device memory. Results are the same as one grid solved
  * alone with mpn_create/mpn_propagate/mpn_trace (bit for bit).
  * ------------------------------------------------------------------------ */
 typedef struct mpn_batch mpn_batch;
@@ -230,6 +277,7 @@ typedef struct {
     float last_round_ms;        /* device time of the last round's propagation */
     int32_t blocks;             /* persistent blocks per launch */
     int32_t admitted, running, done, failed;
+    int32_t graph;              /* 1: rounds replay a captured CUDA graph */
 } mpn_batch_stats_t;
 
 /* budget_bytes >= 1 MiB: the arena; variant: compiled tile shape 0 or 1

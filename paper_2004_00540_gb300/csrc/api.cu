@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include <cuda_runtime.h>
@@ -49,6 +50,7 @@ bool is_device_ptr(const void *p) {
 
 mpn_status from_cuda(cudaError_t e) {
     if (e == cudaSuccess) return MPN_OK;
+    mpn::note_cuda_error(e);
     if (e == cudaErrorMemoryAllocation) return MPN_ENOMEM;
     return MPN_ECUDA;
 }
@@ -72,6 +74,64 @@ mpn_status from_err_bits(uint32_t e) {
 
 namespace mpn {
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+thread_local cudaError_t g_last_error = cudaSuccess;
+void note_cuda_error(cudaError_t e) { g_last_error = e; }
+
+// Autotuner table: per size bucket, the fastest depth measured for each tile
+// shape and the fastest (shape, depth) overall.
+namespace {
+constexpr int kBuckets = 33, kMaxVariants = 16;
+struct TuneTable {
+    std::mutex mu;
+    int depth[kBuckets][kMaxVariants] = {};
+    float ms[kBuckets][kMaxVariants] = {};
+    int best_v[kBuckets], best_d[kBuckets] = {};
+    float best_ms[kBuckets] = {};
+    TuneTable() {
+        for (int b = 0; b < kBuckets; ++b) best_v[b] = -1;
+    }
+};
+TuneTable g_tune;
+
+int bucket_of(int H, int W) {
+    int m = H > W ? H : W, b = 0;
+    while ((1 << b) < m && b < kBuckets - 1) ++b;
+    return b;
+}
+}  // namespace
+
+bool tune_lookup(int H, int W, int variant, int *depth) {
+    if (variant < 0 || variant >= kMaxVariants) return false;
+    std::lock_guard<std::mutex> lk(g_tune.mu);
+    const int b = bucket_of(H, W);
+    if (!g_tune.depth[b][variant]) return false;
+    *depth = g_tune.depth[b][variant];
+    return true;
+}
+
+bool tune_best(int H, int W, int *variant, int *depth) {
+    std::lock_guard<std::mutex> lk(g_tune.mu);
+    const int b = bucket_of(H, W);
+    if (g_tune.best_v[b] < 0) return false;
+    *variant = g_tune.best_v[b];
+    *depth = g_tune.best_d[b];
+    return true;
+}
+
+static void tune_record(int H, int W, int variant, int depth, float ms) {
+    std::lock_guard<std::mutex> lk(g_tune.mu);
+    const int b = bucket_of(H, W);
+    if (!g_tune.depth[b][variant] || ms < g_tune.ms[b][variant]) {
+        g_tune.depth[b][variant] = depth;
+        g_tune.ms[b][variant] = ms;
+    }
+    if (g_tune.best_v[b] < 0 || ms < g_tune.best_ms[b]) {
+        g_tune.best_v[b] = variant;
+        g_tune.best_d[b] = depth;
+        g_tune.best_ms[b] = ms;
+    }
+}
 }  // namespace mpn
 
 struct mpn_ctx {
@@ -143,8 +203,13 @@ mpn_status configure(mpn_ctx *c, int variant, int depth) {
     return MPN_OK;
 }
 
-// Default tiling: the 256 x 256-cell region (192-cell interior), depth 32.
-mpn_status auto_configure(mpn_ctx *c) { return configure(c, 0, 32); }
+// Automatic tiling: the autotuner's choice for this size bucket if one was
+// measured, else the 128-row x 256-cell region at depth 32.
+mpn_status auto_configure(mpn_ctx *c) {
+    int v = 0, d = 32;
+    if (tune_best(c->H, c->W, &v, &d) && configure(c, v, d) == MPN_OK) return MPN_OK;
+    return configure(c, 0, 32);
+}
 
 mpn_status alloc_planes(mpn_ctx *c) {
     const size_t pw = c->plane_words() * sizeof(uint32_t);
@@ -275,6 +340,10 @@ const char *mpn_status_str(mpn_status s) {
 }
 
 uint64_t mpn_launch_count(void) { return g_launches.load(); }
+
+const char *mpn_last_error(void) {
+    return mpn::g_last_error == cudaSuccess ? "" : cudaGetErrorString(mpn::g_last_error);
+}
 
 mpn_status mpn_create(const uint8_t *mask, int32_t H, int32_t W, int32_t dist_bits, void *stream,
                       mpn_ctx **out) {
@@ -462,7 +531,7 @@ mpn_status mpn_get_activity(mpn_ctx *c, uint32_t L, int32_t *dst, int32_t on_dev
 }
 
 static mpn_status trace_prepare(mpn_ctx *c, const uint32_t *starts, int32_t n,
-                                const uint32_t **ds, uint64_t *total) {
+                                const uint32_t **ds, uint64_t *total, bool euclid = false) {
     if (!c || n < 0 || (n > 0 && !starts)) return MPN_EINVAL;
     mpn_status st = finish_propagate(c);
     if (st != MPN_OK) return st;
@@ -482,6 +551,9 @@ static mpn_status trace_prepare(mpn_ctx *c, const uint32_t *starts, int32_t n,
     if (n > 0) {
         MPN_TRY(launch_trace_lengths(c->grid(), c->dist_bits, *ds, n, (uint64_t *)c->offsets.p,
                                      (int8_t *)c->status.p, ctl, c->stream));
+        if (euclid)   // straightened lengths replace d + 1
+            MPN_TRY(launch_euclid(c->grid(), c->dist_bits, *ds, n, (uint64_t *)c->offsets.p,
+                                  (const int8_t *)c->status.p, nullptr, false, c->stream, &ctl->err));
         MPN_TRY(launch_scan((uint64_t *)c->offsets.p, n, c->stream));
     }
     uint32_t err = 0;
@@ -505,12 +577,12 @@ mpn_status mpn_trace_lengths(mpn_ctx *c, const uint32_t *starts, int32_t n, uint
     return from_cuda(cudaStreamSynchronize(c->stream));
 }
 
-mpn_status mpn_trace(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *offsets,
-                     uint32_t *cells, uint64_t cells_cap, int8_t *status) {
+static mpn_status trace_any(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *offsets,
+                            uint32_t *cells, uint64_t cells_cap, int8_t *status, bool euclid) {
     if (!offsets || (n > 0 && !status)) return MPN_EINVAL;
     const uint32_t *ds = nullptr;
     uint64_t total = 0;
-    mpn_status st = trace_prepare(c, starts, n, &ds, &total);
+    mpn_status st = trace_prepare(c, starts, n, &ds, &total, euclid);
     if (st != MPN_OK) return st;
     const bool off_dev = is_device_ptr(offsets), st_dev = n > 0 && is_device_ptr(status);
     MPN_TRY(cudaMemcpyAsync(offsets, c->offsets.p, (size_t)(n + 1) * sizeof(uint64_t),
@@ -532,8 +604,12 @@ mpn_status mpn_trace(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *of
     }
     Ctl *ctl = (Ctl *)c->ctl.p;
     MPN_TRY(cudaEventRecord(c->ev[4], c->stream));
-    MPN_TRY(launch_trace(c->grid(), c->dist_bits, ds, n, (const uint64_t *)c->offsets.p,
-                         (const int8_t *)c->status.p, dcells, c->stream, &ctl->err));
+    if (euclid)
+        MPN_TRY(launch_euclid(c->grid(), c->dist_bits, ds, n, (uint64_t *)c->offsets.p,
+                              (const int8_t *)c->status.p, dcells, true, c->stream, &ctl->err));
+    else
+        MPN_TRY(launch_trace(c->grid(), c->dist_bits, ds, n, (const uint64_t *)c->offsets.p,
+                             (const int8_t *)c->status.p, dcells, c->stream, &ctl->err));
     MPN_TRY(cudaEventRecord(c->ev[5], c->stream));
     c->ev_trace = true;
     if (total > 0 && !cells_dev)
@@ -543,6 +619,80 @@ mpn_status mpn_trace(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *of
     MPN_TRY(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     MPN_TRY(cudaStreamSynchronize(c->stream));
     if (err) return (err & ERR_TRACE) ? MPN_ECUDA : from_err_bits(err);
+    return MPN_OK;
+}
+
+mpn_status mpn_trace(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *offsets,
+                     uint32_t *cells, uint64_t cells_cap, int8_t *status) {
+    return trace_any(c, starts, n, offsets, cells, cells_cap, status, false);
+}
+
+mpn_status mpn_trace_euclid(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *offsets,
+                            uint32_t *cells, uint64_t cells_cap, int8_t *status) {
+    return trace_any(c, starts, n, offsets, cells, cells_cap, status, true);
+}
+
+mpn_status mpn_nearest_targets(mpn_ctx *c, const uint32_t *starts, int32_t n, uint32_t *target,
+                               uint32_t *dist) {
+    if (!target) return MPN_EINVAL;
+    const uint32_t *ds = nullptr;
+    uint64_t total = 0;
+    mpn_status st = trace_prepare(c, starts, n, &ds, &total);
+    if (st != MPN_OK || n == 0) return st;
+    const bool t_dev = is_device_ptr(target), d_dev = dist && is_device_ptr(dist);
+    uint32_t *dt = target, *dd = dist;
+    if (!t_dev || (dist && !d_dev)) {
+        MPN_TRY(c->cells.ensure((size_t)n * 8));
+        if (!t_dev) dt = (uint32_t *)c->cells.p;
+        if (dist && !d_dev) dd = (uint32_t *)c->cells.p + n;
+    }
+    Ctl *ctl = (Ctl *)c->ctl.p;
+    MPN_TRY(cudaEventRecord(c->ev[4], c->stream));
+    MPN_TRY(launch_nearest(c->grid(), c->dist_bits, ds, n, (const int8_t *)c->status.p, dt, dd,
+                           c->stream, &ctl->err));
+    MPN_TRY(cudaEventRecord(c->ev[5], c->stream));
+    c->ev_trace = true;
+    if (!t_dev) MPN_TRY(cudaMemcpyAsync(target, dt, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (dist && !d_dev) MPN_TRY(cudaMemcpyAsync(dist, dd, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+    uint32_t err = 0;
+    MPN_TRY(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    MPN_TRY(cudaStreamSynchronize(c->stream));
+    if (err) return (err & ERR_TRACE) ? MPN_ECUDA : from_err_bits(err);
+    return MPN_OK;
+}
+
+mpn_status mpn_autotune(mpn_ctx *c, const uint32_t *targets, int32_t n, int32_t *variant,
+                        int32_t *depth, float *best_ms) {
+    if (!c || !targets || n < 1) return MPN_EINVAL;
+    static const int kDepths[] = {8, 12, 16, 24, 32};
+    int bv = -1, bd = 0;
+    float bms = 0.f;
+    for (int v = 0; v < num_variants(); ++v) {
+        for (int d : kDepths) {
+            if (configure(c, v, d) != MPN_OK) continue;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {   // the first run warms caches and clocks
+                uint32_t layers = 0;
+                mpn_status st = mpn_propagate(c, targets, n, 0, &layers);
+                if (st != MPN_OK) return st;
+                MPN_TRY(cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]));
+            }
+            mpn::tune_record(c->H, c->W, v, d, ms);
+            if (bv < 0 || ms < bms) {
+                bv = v;
+                bd = d;
+                bms = ms;
+            }
+        }
+    }
+    if (bv < 0) return MPN_ECUDA;
+    mpn_status st = configure(c, bv, bd);
+    if (st != MPN_OK) return st;
+    c->auto_tune = false;
+    c->propagated = false;
+    if (variant) *variant = bv;
+    if (depth) *depth = bd;
+    if (best_ms) *best_ms = bms;
     return MPN_OK;
 }
 
@@ -563,9 +713,14 @@ mpn_status mpn_get_stats(mpn_ctx *c, mpn_stats *out) {
     out->layers = c->last_layers;
     out->sweeps = c->last_ctl.sweeps;
     out->tile_visits = c->last_ctl.visits;
-    if (c->ev_enc) cudaEventElapsedTime(&c->ms_encode, c->ev[0], c->ev[1]);
-    if (c->ev_prop) cudaEventElapsedTime(&c->ms_propagate, c->ev[2], c->ev[3]);
-    if (c->ev_trace) cudaEventElapsedTime(&c->ms_trace, c->ev[4], c->ev[5]);
+    // timings are best effort: a failed query leaves the last value and no
+    // stale error behind for the next launch check
+    if (c->ev_enc && cudaEventElapsedTime(&c->ms_encode, c->ev[0], c->ev[1]) != cudaSuccess)
+        cudaGetLastError();
+    if (c->ev_prop && cudaEventElapsedTime(&c->ms_propagate, c->ev[2], c->ev[3]) != cudaSuccess)
+        cudaGetLastError();
+    if (c->ev_trace && cudaEventElapsedTime(&c->ms_trace, c->ev[4], c->ev[5]) != cudaSuccess)
+        cudaGetLastError();
     out->ms_encode = c->ms_encode;
     out->ms_propagate = c->ms_propagate;
     out->ms_trace = c->ms_trace;
@@ -574,7 +729,7 @@ mpn_status mpn_get_stats(mpn_ctx *c, mpn_stats *out) {
 
 void mpn_destroy(mpn_ctx *c) {
     if (!c) return;
-    if (c->stream || true) cudaStreamSynchronize(c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) cudaGetLastError();
     DevBuf *bufs[] = {&c->free_bits, &c->vis, &c->nb0, &c->nb1, &c->dist, &c->ctl, &c->tiles,
                       &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
                       &c->cells, &c->activity};

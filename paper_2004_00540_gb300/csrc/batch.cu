@@ -228,6 +228,15 @@ __global__ void k_check_inputs(const uint32_t *free_bits, int H, int W, int P,
     if (i < ns && starts[i] >= N) atomicOr(flag, 4u);
 }
 
+// Round preparation on the device, so that the round itself has fixed
+// launch parameters and can be replayed from a CUDA graph: a fresh claim
+// counter for the round's first sweep and a clear error word.
+__global__ void k_round_prep(BatchCtl *bc) {
+    const uint32_t s = bc->next_sweep;
+    bc->c.work[s % 3] = 0u;
+    bc->c.err = 0u;
+}
+
 __global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         p[i] = v;
@@ -348,6 +357,8 @@ struct mpn_batch {
     uint64_t next_ticket = 1;
     uint32_t next_sweep = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::map<uint32_t, cudaGraphExec_t> graphs;   // one captured round per max_sweeps value
+    bool use_graph = true;
     float last_round_ms = 0.f;
     uint64_t rounds = 0, sweeps_total = 0;
 };
@@ -356,6 +367,7 @@ namespace {
 
 mpn_status cuda_st(cudaError_t e) {
     if (e == cudaSuccess) return MPN_OK;
+    note_cuda_error(e);
     return e == cudaErrorMemoryAllocation ? MPN_ENOMEM : MPN_ECUDA;
 }
 
@@ -377,12 +389,12 @@ bool dev_ptr(const void *p) {
 
 void *arena_at(mpn_batch *b, size_t off) { return (char *)b->arena + off; }
 
-// Depth used for a grid: the override if set, else 32 (interior 64 rows of
-// the 128-row region); variant 1 (256 rows) uses 32 as well.
+// Depth used for a grid: the override if set, else the autotuner's pick for
+// its size bucket and the batch's tile shape, else 32.
 int depth_for(mpn_batch *b, int H, int W) {
-    (void)H;
-    (void)W;
     if (b->depth_override) return b->depth_override;
+    int d = 0;
+    if (tune_lookup(H, W, b->variant, &d)) return d;   // the autotuner's pick for this size
     return 32;
 }
 
@@ -559,6 +571,73 @@ mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_
     return MPN_OK;
 }
 
+// The round: device-side preparation, then the cooperative persistent launch.
+static cudaError_t enqueue_round(mpn_batch *b, const BatchParams &p) {
+    cudaStream_t st = b->stream;
+    k_round_prep<<<1, 1, 0, st>>>(b->d_bc);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // external records, so that they time the round also when it is captured
+    e = cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal);
+    if (e != cudaSuccess) return e;
+    const VariantDesc vd = variant_desc(b->variant);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->blocks);
+    cfg.blockDim = dim3(vd.nwarps * 32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BatchParams pp = p;
+    void *args[] = {&pp};
+    e = cudaLaunchKernelExC(&cfg, batch_fn(b->variant), args);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal);
+}
+
+// Run one round from a CUDA graph captured the first time this max_sweeps
+// value is used (launch parameters are fixed: everything that changes from
+// round to round lives in device memory).
+static cudaError_t run_round(mpn_batch *b, const BatchParams &p) {
+    if (!b->use_graph) {
+        count_launch(2);
+        return enqueue_round(b, p);
+    }
+    auto it = b->graphs.find(p.round_sweeps);
+    if (it == b->graphs.end()) {
+        cudaStream_t cs = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        cudaStream_t keep = b->stream;
+        b->stream = cs;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue_round(b, p);
+            e = cudaStreamEndCapture(cs, &g);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        b->stream = keep;
+        cudaStreamDestroy(cs);
+        cudaGraphExec_t ge = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            // capture not available: run rounds as plain launches from now on
+            cudaGetLastError();
+            b->use_graph = false;
+            count_launch(2);
+            return enqueue_round(b, p);
+        }
+        it = b->graphs.emplace(p.round_sweeps, ge).first;
+    }
+    count_launch(2);
+    return cudaGraphLaunch(it->second, b->stream);
+}
+
 static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t *cells) {
     char *res = (char *)arena_at(b, m.res_off);
     GridDev g;
@@ -717,21 +796,13 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, 
     }
     int running = 0;
     for (auto &kv : b->mazes) running += kv.second.state == MState::Running;
-    if (running > 0) {
-        // a fresh work counter for the round's first sweep
-        B_TRY(cudaMemsetAsync(&b->d_bc->c.work[b->next_sweep % 3], 0, 4, st));
-        B_TRY(cudaMemsetAsync(&b->d_bc->c.err, 0, 4, st));
-        B_TRY(cudaEventRecord(b->ev0, st));
-        void *args[] = {&p};
-        const VariantDesc vd = variant_desc(b->variant);
-        count_launch();
-        B_TRY(cudaLaunchCooperativeKernel(batch_fn(b->variant), dim3(b->blocks), dim3(vd.nwarps * 32),
-                                          args, 0, st));
-        B_TRY(cudaEventRecord(b->ev1, st));
-    }
+    if (running > 0) B_TRY(run_round(b, p));
     mpn_status s = finish_round(b);
     if (running > 0) {
-        cudaEventElapsedTime(&b->last_round_ms, b->ev0, b->ev1);
+        if (cudaEventElapsedTime(&b->last_round_ms, b->ev0, b->ev1) != cudaSuccess) {
+            cudaGetLastError();   // leave no stale error for the next launch check
+            b->last_round_ms = 0.f;
+        }
         b->rounds++;
         b->sweeps_total += b->h_bc->c.sweeps;
     }
@@ -837,6 +908,7 @@ mpn_status mpn_batch_stats(mpn_batch *b, mpn_batch_stats_t *out) {
     out->sweeps = b->sweeps_total;
     out->last_round_ms = b->last_round_ms;
     out->blocks = b->blocks;
+    out->graph = b->use_graph ? 1 : 0;
     for (auto &kv : b->mazes) {
         const MState s = kv.second.state;
         out->admitted += s == MState::Admitted;
@@ -861,6 +933,7 @@ void mpn_batch_destroy(mpn_batch *b) {
     if (b->h_bc) cudaFreeHost(b->h_bc);
     if (b->h_jobs) cudaFreeHost(b->h_jobs);
     if (b->h_flag) cudaFreeHost(b->h_flag);
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;

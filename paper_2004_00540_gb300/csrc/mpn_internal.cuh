@@ -67,8 +67,16 @@ struct VariantDesc {
     int minb;     // blocks per SM the register budget aims at
 };
 
+// ---- autotuner table (api.cu): best depth per (size bucket, variant) ----
+// bucket = ceil(log2(max(H, W))); returns false when nothing was measured.
+bool tune_lookup(int H, int W, int variant, int *depth);
+bool tune_best(int H, int W, int *variant, int *depth);
+
 // ---- launch helpers implemented in the .cu files ----
 void count_launch(int n = 1);
+// remember the last CUDA error a library call hit (per host thread), for
+// mpn_last_error
+void note_cuda_error(cudaError_t e);
 
 int num_variants();
 VariantDesc variant_desc(int v);
@@ -96,5 +104,11 @@ cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts
                          cudaStream_t st, uint32_t *err);
 cudaError_t launch_activity(const GridDev &g, int dist_bits, uint32_t L, int32_t *out,
                             cudaStream_t st);
+cudaError_t launch_nearest(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                           const int8_t *status, uint32_t *ends, uint32_t *ends_d, cudaStream_t st,
+                           uint32_t *err);
+cudaError_t launch_euclid(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                          uint64_t *offsets, const int8_t *status, uint32_t *cells, bool write,
+                          cudaStream_t st, uint32_t *err);
 
 }  // namespace mpn

@@ -98,16 +98,26 @@ __global__ void k_scan(uint64_t *a, int n) {
     }
 }
 
-template <typename DT>
+// CELLS: write the whole path at offsets[i]; otherwise write only the cell
+// the walk ends at (the target reached) to ends[i] and the start's distance
+// to ends_d[i] (0xFFFFFFFF for both when the start has no path).
+template <typename DT, bool CELLS>
 __global__ void __launch_bounds__(kTraceWarps * 32)
     k_trace(GridDev g, const uint32_t *__restrict__ starts, int n,
             const uint64_t *__restrict__ offsets, const int8_t *__restrict__ status,
-            uint32_t *__restrict__ cells, uint32_t *err) {
+            uint32_t *__restrict__ cells, uint32_t *__restrict__ ends, uint32_t *__restrict__ ends_d,
+            uint32_t *err) {
     __shared__ DT win[kTraceWarps][kWin * kWinPitch];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int i = blockIdx.x * kTraceWarps + wl;
     if (i >= n) return;                         // whole warp leaves together
-    if (status[i] != MPN_PATH_OK) return;
+    if (status[i] != MPN_PATH_OK) {
+        if (!CELLS && lane == 0) {
+            ends[i] = 0xffffffffu;
+            if (ends_d) ends_d[i] = 0xffffffffu;
+        }
+        return;
+    }
     const DT *dist = reinterpret_cast<const DT *>(g.dist);
     const DT INF = (DT)~(DT)0;
     DT *wb = win[wl];
@@ -116,10 +126,11 @@ __global__ void __launch_bounds__(kTraceWarps * 32)
     const int my_dx = (lane == 0 || lane == 3 || lane == 5) ? -1 : ((lane == 1 || lane == 6) ? 0 : 1);
 
     uint32_t c = starts[i];
-    uint64_t o = offsets[i];
+    uint64_t o = CELLS ? offsets[i] : 0ull;
     int cy = (int)(c / (uint32_t)g.W), cx = (int)(c % (uint32_t)g.W);
     uint32_t d = (uint32_t)dist[c];
-    if (lane == 0) cells[o] = c;
+    const uint32_t d0 = d;
+    if (CELLS && lane == 0) cells[o] = c;
     while (d > 0) {
         const int wy0 = cy - kWin / 2, wx0 = cx - kWin / 2;
         const int x = wx0 + lane;
@@ -145,12 +156,120 @@ __global__ void __launch_bounds__(kTraceWarps * 32)
             lx += __shfl_sync(0xffffffffu, my_dx, q);
             --d;
             ++o;
-            if (lane == 0) cells[o] = (uint32_t)((wy0 + ly) * g.W + (wx0 + lx));
+            if (CELLS && lane == 0) cells[o] = (uint32_t)((wy0 + ly) * g.W + (wx0 + lx));
         }
         __syncwarp();
         cy = wy0 + ly;
         cx = wx0 + lx;
     }
+    if (!CELLS && lane == 0) {
+        ends[i] = (uint32_t)cy * (uint32_t)g.W + (uint32_t)cx;
+        if (ends_d) ends_d[i] = d0;
+    }
+}
+
+// Euclidean path reconstruction (Eq. 1 and the straightening rule after it),
+// one warp per start, in the same 32 x 32 shared-memory windows as k_trace.
+// Each step tests all candidate moves at once: lanes 0-3 the 4-neighbours in
+// Eq. 1's order (left, right, up, down) for distance d - 1; lanes 4-19 the
+// corner rule (4-neighbour q with distance d that is 4-adjacent, through r,
+// to a cell with d - 1); lanes 20-27 the 8-neighbours for d - 1 (both corners
+// blocked). The first hit in that order is taken. Straightening runs on the
+// fly with a one-point delay: a point is dropped when the last kept point and
+// the next point are sqrt(2) apart. COUNT pass: only the kept length; WRITE
+// pass: the cells at the offsets of the count pass.
+template <typename DT, bool WRITE>
+__global__ void __launch_bounds__(kTraceWarps * 32)
+    k_euclid(GridDev g, const uint32_t *__restrict__ starts, int n, uint64_t *__restrict__ offsets,
+             const int8_t *__restrict__ status, uint32_t *__restrict__ cells, uint32_t *err) {
+    __shared__ DT win[kTraceWarps][kWin * kWinPitch];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int i = blockIdx.x * kTraceWarps + wl;
+    if (i >= n) return;
+    if (status[i] != MPN_PATH_OK) {
+        if (!WRITE && lane == 0) offsets[i + 1] = 0ull;
+        return;
+    }
+    const DT *dist = reinterpret_cast<const DT *>(g.dist);
+    const DT INF = (DT)~(DT)0;
+    DT *wb = win[wl];
+    // per-lane candidate geometry: (qy, qx) first move, (ry, rx) second
+    int qy = 0, qx = 0, ry = 0, rx = 0;
+    {
+        const int EY[4] = {0, 0, -1, 1}, EX[4] = {-1, 1, 0, 0};
+        const int DY8[8] = {-1, -1, -1, 0, 0, 1, 1, 1}, DX8[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+        if (lane < 4) { qy = EY[lane]; qx = EX[lane]; }
+        else if (lane < 20) { qy = EY[(lane - 4) >> 2]; qx = EX[(lane - 4) >> 2];
+                              ry = EY[(lane - 4) & 3]; rx = EX[(lane - 4) & 3]; }
+        else if (lane < 28) { qy = DY8[lane - 20]; qx = DX8[lane - 20]; }
+    }
+    const uint32_t s0 = starts[i];
+    uint64_t o = WRITE ? offsets[i] : 0ull;
+    uint64_t kept = 0;
+    int cy = (int)(s0 / (uint32_t)g.W), cx = (int)(s0 % (uint32_t)g.W);
+    uint32_t d = (uint32_t)dist[s0];
+    // straightening state: last kept point, pending point
+    int ky = cy, kx = cx, py = -1, px = -1;
+    bool has_pending = false;
+    if (WRITE && lane == 0) cells[o] = s0;
+    ++kept;
+    while (d > 0) {
+        const int wy0 = cy - kWin / 2, wx0 = cx - kWin / 2;
+        const int x = wx0 + lane;
+#pragma unroll 8
+        for (int r = 0; r < kWin; ++r) {
+            const int y = wy0 + r;
+            DT v = INF;
+            if (y >= 0 && y < g.H && x >= 0 && x < g.W) v = dist[(size_t)y * g.W + x];
+            wb[r * kWinPitch + lane] = v;
+        }
+        __syncwarp();
+        int ly = cy - wy0, lx = cx - wx0;
+        while (d > 0 && ly >= 2 && ly <= kWin - 3 && lx >= 2 && lx <= kWin - 3) {
+            bool hit = false;
+            if (lane < 4 || (lane >= 20 && lane < 28)) {
+                hit = (uint32_t)wb[(ly + qy) * kWinPitch + lx + qx] == d - 1u;
+            } else if (lane < 20) {
+                hit = (uint32_t)wb[(ly + qy) * kWinPitch + lx + qx] == d &&
+                      (uint32_t)wb[(ly + qy + ry) * kWinPitch + lx + qx + rx] == d - 1u;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            unsigned pick = m & 0xfu;
+            if (!pick) pick = m & 0xffff0u;
+            if (!pick) pick = m & 0x0ff00000u;
+            if (!pick) {
+                if (lane == 0) atomicOr(err, ERR_TRACE);
+                return;
+            }
+            const int q = __ffs(pick) - 1;
+            const int sy = __shfl_sync(0xffffffffu, qy, q), sx = __shfl_sync(0xffffffffu, qx, q);
+            ly += sy;
+            lx += sx;
+            if (q < 4 || q >= 20) --d;   // a corner move keeps the distance
+            // straightening with a one-point delay
+            const int ny = wy0 + ly, nx = wx0 + lx;
+            if (has_pending) {
+                const int ay = ky - ny, ax = kx - nx;
+                if (ay * ay + ax * ax != 2) {      // keep the pending point
+                    if (WRITE && lane == 0) cells[o + kept] = (uint32_t)(py * g.W + px);
+                    ++kept;
+                    ky = py;
+                    kx = px;
+                }
+            }
+            py = ny;
+            px = nx;
+            has_pending = true;
+        }
+        __syncwarp();
+        cy = wy0 + ly;
+        cx = wx0 + lx;
+    }
+    if (has_pending) {   // the last point (a target) is always kept
+        if (WRITE && lane == 0) cells[o + kept] = (uint32_t)(py * g.W + px);
+        ++kept;
+    }
+    if (!WRITE && lane == 0) offsets[i + 1] = kept;
 }
 
 template <typename DT>
@@ -194,9 +313,43 @@ cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts
     const int nb = (n + kTraceWarps - 1) / kTraceWarps;
     count_launch();
     if (dist_bits == 16)
-        k_trace<uint16_t><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, offsets, status, cells, err);
+        k_trace<uint16_t, true><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, offsets, status, cells,
+                                                                 nullptr, nullptr, err);
     else
-        k_trace<uint32_t><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, offsets, status, cells, err);
+        k_trace<uint32_t, true><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, offsets, status, cells,
+                                                                 nullptr, nullptr, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nearest(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                           const int8_t *status, uint32_t *ends, uint32_t *ends_d, cudaStream_t st,
+                           uint32_t *err) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = (n + kTraceWarps - 1) / kTraceWarps;
+    count_launch();
+    if (dist_bits == 16)
+        k_trace<uint16_t, false><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, nullptr, status, nullptr,
+                                                                  ends, ends_d, err);
+    else
+        k_trace<uint32_t, false><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, nullptr, status, nullptr,
+                                                                  ends, ends_d, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euclid(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                          uint64_t *offsets, const int8_t *status, uint32_t *cells, bool write,
+                          cudaStream_t st, uint32_t *err) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = (n + kTraceWarps - 1) / kTraceWarps;
+    const dim3 tb(kTraceWarps * 32);
+    count_launch();
+    if (dist_bits == 16) {
+        if (write) k_euclid<uint16_t, true><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, cells, err);
+        else k_euclid<uint16_t, false><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, cells, err);
+    } else {
+        if (write) k_euclid<uint32_t, true><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, cells, err);
+        else k_euclid<uint32_t, false><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, cells, err);
+    }
     return cudaGetLastError();
 }
 

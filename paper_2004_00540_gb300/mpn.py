@@ -30,14 +30,18 @@ EXPORTS = (
     "mpn_variant_info", "mpn_get_stats", "mpn_launch_count", "mpn_propagate_noalloc",
     "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_submit", "mpn_batch_run",
     "mpn_batch_poll", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
-    "mpn_batch_stats", "mpn_batch_destroy",
+    "mpn_batch_stats", "mpn_batch_destroy", "mpn_autotune", "mpn_trace_euclid",
+    "mpn_nearest_targets", "mpn_last_error",
 )
 MPN_BATCH_PENDING, MPN_BATCH_DONE, MPN_BATCH_FAILED = 0, 1, 2
 
 
 class MPNError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__(f"{what}: {status_name(status)} ({status})")
+        detail = ""
+        if status in (2, 3) and _lib is not None:
+            detail = _lib.mpn_last_error().decode()
+        super().__init__(f"{what}: {status_name(status)} ({status})" + (f" [{detail}]" if detail else ""))
         self.status = status
 
 
@@ -61,7 +65,7 @@ class mpn_batch_stats_t(ctypes.Structure):
         ("rounds", ctypes.c_uint64), ("sweeps", ctypes.c_uint64),
         ("last_round_ms", ctypes.c_float), ("blocks", ctypes.c_int32),
         ("admitted", ctypes.c_int32), ("running", ctypes.c_int32), ("done", ctypes.c_int32),
-        ("failed", ctypes.c_int32),
+        ("failed", ctypes.c_int32), ("graph", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -118,6 +122,11 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
             "mpn_batch_release": ([vp, u64], ctypes.c_int),
             "mpn_batch_stats": ([vp, ctypes.POINTER(mpn_batch_stats_t)], ctypes.c_int),
             "mpn_batch_destroy": ([vp], None),
+            "mpn_trace_euclid": ([vp, vp, i32, vp, vp, u64, vp], ctypes.c_int),
+            "mpn_nearest_targets": ([vp, vp, i32, vp, vp], ctypes.c_int),
+            "mpn_last_error": ([], ctypes.c_char_p),
+            "mpn_autotune": ([vp, vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                              ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -237,6 +246,24 @@ def mpn_trace(ctx, starts, offsets, cells, cells_cap: int, status):
     return st
 
 
+def mpn_trace_euclid(ctx, starts, offsets, cells, cells_cap: int, status):
+    """Euclidean reconstruction; returns MPN_OK or MPN_ENOMEM (offsets filled)."""
+    n = int(starts.numel() if hasattr(starts, "numel") else np.asarray(starts).size)
+    st = load().mpn_trace_euclid(ctx, _ptr(starts)[0], n, _ptr(offsets)[0], _ptr(cells)[0],
+                                 cells_cap, _ptr(status)[0])
+    if st not in (MPN_OK, MPN_ENOMEM):
+        raise MPNError(st, "mpn_trace_euclid")
+    return st
+
+
+def mpn_nearest_targets(ctx, starts, target, dist=None):
+    n = int(starts.numel() if hasattr(starts, "numel") else np.asarray(starts).size)
+    _check(load().mpn_nearest_targets(ctx, _ptr(starts)[0], n, _ptr(target)[0],
+                                      _ptr(dist)[0] if dist is not None else None),
+           "mpn_nearest_targets")
+    return target
+
+
 def mpn_sync(ctx):
     _check(load().mpn_sync(ctx), "mpn_sync")
 
@@ -266,6 +293,15 @@ def mpn_get_stats(ctx) -> dict:
     s = mpn_stats()
     _check(load().mpn_get_stats(ctx, ctypes.byref(s)), "mpn_get_stats")
     return s.as_dict()
+
+
+def mpn_autotune(ctx, targets):
+    """Measure every tile shape x depth; returns (variant, depth, ms)."""
+    n = int(targets.numel() if hasattr(targets, "numel") else np.asarray(targets).size)
+    v, d, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().mpn_autotune(ctx, _ptr(targets)[0], n, ctypes.byref(v), ctypes.byref(d),
+                               ctypes.byref(ms)), "mpn_autotune")
+    return v.value, d.value, ms.value
 
 
 def mpn_launch_count() -> int:
@@ -326,6 +362,10 @@ class Planner:
     def set_tuning(self, variant: int, depth: int):
         mpn_set_tuning(self.ctx, variant, depth)
 
+    def autotune(self, targets):
+        t = np.ascontiguousarray(targets, np.uint32) if not hasattr(targets, "data_ptr") else targets
+        return mpn_autotune(self.ctx, t)
+
     def propagate(self, targets, max_layers: int = 0, plain: bool = False, check_every: int = 1):
         t = np.ascontiguousarray(targets, np.uint32) if not hasattr(targets, "data_ptr") else targets
         if plain:
@@ -353,6 +393,28 @@ class Planner:
         st = mpn_trace(self.ctx, s, offsets, cells, total, status)
         if st != MPN_OK:
             raise MPNError(st, "mpn_trace")
+        return Paths(offsets, cells[:total], status[:n])
+
+    def nearest_targets(self, starts):
+        """(target cell, distance) per start; 0xFFFFFFFF where there is no path."""
+        s = np.ascontiguousarray(starts, np.uint32)
+        t = np.empty(s.size, np.uint32)
+        d = np.empty(s.size, np.uint32)
+        mpn_nearest_targets(self.ctx, s, t, d)
+        return t, d
+
+    def trace_euclid(self, starts) -> Paths:
+        s = np.ascontiguousarray(starts, np.uint32)
+        n = s.size
+        offsets = np.zeros(n + 1, np.uint64)
+        status = np.zeros(max(n, 1), np.int8)
+        cells = np.zeros(1, np.uint32)
+        mpn_trace_euclid(self.ctx, s, offsets, cells, 0, status)     # sizes first
+        total = int(offsets[-1])
+        cells = np.zeros(max(total, 1), np.uint32)
+        st = mpn_trace_euclid(self.ctx, s, offsets, cells, total, status)
+        if st != MPN_OK:
+            raise MPNError(st, "mpn_trace_euclid")
         return Paths(offsets, cells[:total], status[:n])
 
     def stats(self) -> dict:

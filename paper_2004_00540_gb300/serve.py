@@ -54,6 +54,11 @@ class ServeReport:
         }
 
 
+def _count(a) -> int:
+    """Element count of a numpy array or a torch tensor."""
+    return int(a.numel()) if hasattr(a, "numel") else int(np.asarray(a).size)
+
+
 def serve(batch: Batch, requests: list, round_sweeps: int = 64, keep_results: bool = False,
           clock=time.perf_counter) -> ServeReport:
     """Run every request through the batch as it arrives; returns latencies."""
@@ -84,7 +89,7 @@ def serve(batch: Batch, requests: list, round_sweeps: int = 64, keep_results: bo
                     continue
                 i = in_flight.pop(tk)
                 if st == MPN_BATCH_DONE:
-                    _, paths, _ = batch.result(tk, requests[i].starts.size, want_dist=False)
+                    _, paths, _ = batch.result(tk, _count(requests[i].starts), want_dist=False)
                     if keep_results:
                         rep.results[i] = paths
                 else:

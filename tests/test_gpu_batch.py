@@ -61,6 +61,7 @@ def test_batch_continuous_arrivals_and_short_rounds():
         for tk, i in tickets.items():
             check(b, tk, ws[i])
         assert b.stats()["rounds"] > 3
+        assert b.stats()["graph"] == 1          # rounds replayed from a captured CUDA graph
 
 
 def test_batch_admission_by_memory():

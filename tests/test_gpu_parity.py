@@ -231,3 +231,74 @@ def test_workload_c5_huge_full():
     w = synth.c5_huge()
     stats = assert_parity(w.mask, w.targets, w.starts)
     assert stats["layers"] > 100
+
+
+def test_autotune_records_choice_and_stays_exact():
+    m, t, s = rand_case(1500, 1400, 0.3, 6, 40, 77)
+    with pkg.Planner(m) as pl:
+        v, d, ms = pl.autotune(t)
+        assert 0 <= v < n_variants() and 1 <= d <= max_depth(v) and ms > 0
+        st = pl.stats()
+        assert (st["variant"], st["depth"]) == (v, d)
+        pl.propagate(t)
+        assert np.array_equal(widen(pl.distances()), oracle.bfs(m, t)[0])
+    # a later context of the same size bucket starts from the measured choice
+    m2, t2, s2 = rand_case(1700, 1300, 0.25, 3, 40, 78)
+    with pkg.Planner(m2) as pl:
+        st = pl.stats()
+        assert (st["variant"], st["depth"]) == (v, d)
+    assert_parity(m2, t2, s2)
+
+
+@pytest.mark.parametrize("case", ["empty", "bernoulli", "maze", "c1", "c3"])
+def test_euclid_trace_matches_oracle(case):
+    if case == "empty":
+        m = synth.empty(300, 500)
+        t = np.array([0, 299 * 500 + 499], np.uint32)
+        s = np.random.default_rng(0).integers(0, 300 * 500, 200).astype(np.uint32)
+    elif case == "bernoulli":
+        m, t, s = rand_case(700, 900, 0.3, 3, 300, 31)
+    elif case == "maze":
+        m = synth.dfs_maze(301, 257, 5)
+        t = synth.sample_free(m, 2, 6)
+        s = np.random.default_rng(1).integers(0, 301 * 257, 100).astype(np.uint32)
+    elif case == "c1":
+        w = synth.c1_small()
+        m, t, s = w.mask, w.targets, w.starts
+    else:
+        w = synth.c3_maze_open()
+        m, t, s = w.mask, w.targets, w.starts
+    d, _ = oracle.bfs(m, t)
+    ooff, ocells, ostatus = oracle.euclid_trace(m, d, s)
+    with pkg.Planner(m) as pl:
+        pl.propagate(t)
+        p = pl.trace_euclid(s)
+    assert np.array_equal(p.status, ostatus)
+    assert np.array_equal(p.offsets, ooff)
+    assert np.array_equal(p.cells, ocells)
+
+
+@pytest.mark.parametrize("case", ["bernoulli", "c3"])
+def test_nearest_targets(case):
+    if case == "bernoulli":
+        m, t, s = rand_case(600, 800, 0.3, 12, 500, 41)
+    else:
+        w = synth.c3_maze_open()
+        m, t, s = w.mask, w.targets, w.starts
+    d, _ = oracle.bfs(m, t)
+    off, cells, status = oracle.trace(m, d, s)
+    with pkg.Planner(m) as pl:
+        pl.propagate(t)
+        got_t, got_d = pl.nearest_targets(s)
+    tset = set(int(x) for x in t)
+    for i in range(s.size):
+        if status[i] != 0:
+            assert got_t[i] == 0xFFFFFFFF and got_d[i] == 0xFFFFFFFF
+            continue
+        assert got_t[i] == cells[off[i + 1] - 1] and int(got_t[i]) in tset
+        assert got_d[i] == d.reshape(-1)[s[i]]
+    # the reached target is a nearest one: its own BFS distance to the start
+    # equals the start's multi-source distance
+    for i in np.flatnonzero(status == 0)[:20]:
+        dt, _ = oracle.bfs(m, [int(got_t[i])])
+        assert dt.reshape(-1)[s[i]] == d.reshape(-1)[s[i]]

@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--plain-sample", type=int, default=32,
                     help="mazes timed with one launch per layer (the slow baseline)")
+    ap.add_argument("--fig5", action="store_true",
+                    help="the paper's run-time experiment on empty n x n grids with fixed L")
     return ap.parse_args()
 
 
@@ -125,6 +127,33 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+KERNEL_SOURCES = ("paper_2004_00540_gb300/csrc/wave.cuh", "paper_2004_00540_gb300/csrc/propagate.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_propagate_traffic.json")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per k_propagate launch from the committed ncu capture, or
+    None when the kernel sources changed since it was taken (or no capture
+    exists for this workload)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_sha256") != kernel_source_hash() or t.get("workload") != workload:
+        return None
+    return t.get("dram_bytes_per_launch")
 
 
 def shard(n_items: int, rank: int, world: int):
@@ -274,11 +303,43 @@ def run_batched(args, pkg, torch):
     return out
 
 
+PAPER_FIG5_S_PER_L_N2 = 3.0751e-10   # seconds per layer per cell, GTX 1080 Ti (Results, run-time)
+
+
+def run_fig5(args):
+    """Empty n x n grids, one source in a corner (the paper's worst case), a
+    network of fixed depth L in {0.5n, n, 1.5n, 2n}; device time of the
+    propagation beside the paper's fitted model."""
+    import torch
+    import paper_2004_00540_gb300 as pkg
+    rows = []
+    for n in (500, 1000, 2000, 3000, 4000):
+        m = torch.zeros((n, n), dtype=torch.uint8, device="cuda")
+        t = torch.zeros(1, dtype=torch.int32, device="cuda")
+        with pkg.Planner(m, pkg.MPN_DIST_U32) as pl:
+            for f in (0.5, 1.0, 1.5, 2.0):
+                L = int(f * n)
+                ms = []
+                for rep in range(4):
+                    pl.propagate(t, max_layers=L)
+                    ms.append(pl.stats()["ms_propagate"])
+                best = min(ms[1:])
+                layers = pl.layers
+                paper_s = PAPER_FIG5_S_PER_L_N2 * L * n * n
+                rows.append({"n": n, "L": L, "layers_reached": layers, "ms": best,
+                             "effective_cell_updates_per_s": n * n * L / (best * 1e-3),
+                             "paper_model_s": paper_s, "speedup_vs_paper_model": paper_s / (best * 1e-3)})
+    print(json.dumps({"fig5_empty_grids": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.fig5:
+        return run_fig5(args)
 
     import torch
     import paper_2004_00540_gb300 as pkg
@@ -356,7 +417,7 @@ def main():
     peak, peak_kind = peaks()
     achieved = units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+            "frac": achieved / peak, "traffic": measured_traffic(w.name), "peak_kind": peak_kind,
             "kernel": "k_propagate", "ms_per_launch": prop_avg,
             "note": "algorithmic bytes = 8.125 B per effective cell-update (mask bit + uint32 "
                     "read + write per layer); temporal blocking does each update in registers"}

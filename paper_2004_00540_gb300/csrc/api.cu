@@ -185,6 +185,7 @@ mpn_status configure(mpn_ctx *c, int variant, int depth) {
     const int TY = ry - 2 * depth, TXW = vd.rxw - 2;
     const int wwords = (c->W + 31) / 32;
     const int ntx = (wwords + TXW - 1) / TXW, nty = (c->H + TY - 1) / TY;
+    if (vd.tma && c->dist_bits != 32) return MPN_EINVAL;   // the TMA shape writes uint32 planes
     int bps = 0;
     MPN_TRY(propagate_blocks_per_sm(variant, c->dist_bits, &bps));
     if (bps < 1) return MPN_ECUDA;
@@ -413,7 +414,7 @@ mpn_status mpn_variant_info(int32_t v, int32_t *rows, int32_t *words, int32_t *t
     const VariantDesc d = variant_desc(v);
     if (rows) *rows = d.nwarps * (32 / d.rxw) * d.r;
     if (words) *words = d.rxw;
-    if (threads) *threads = d.nwarps * 32;
+    if (threads) *threads = variant_threads(v);
     return MPN_OK;
 }
 

@@ -63,8 +63,9 @@ struct PropParams {
 struct VariantDesc {
     int rxw;      // region words (lanes per row group)
     int r;        // rows per lane
-    int nwarps;   // warps per block
+    int nwarps;   // warps per block that run the layers
     int minb;     // blocks per SM the register budget aims at
+    int tma;      // 1: one more (producer) warp stages regions with TMA; uint32 planes only
 };
 
 // ---- autotuner table (api.cu): best depth per (size bucket, variant) ----
@@ -80,6 +81,7 @@ void note_cuda_error(cudaError_t e);
 
 int num_variants();
 VariantDesc variant_desc(int v);
+int variant_threads(int v);   // threads per block of variant v
 cudaError_t propagate_blocks_per_sm(int v, int dist_bits, int *out);
 cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int blocks,
                              cudaStream_t st);

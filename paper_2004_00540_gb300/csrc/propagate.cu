@@ -12,7 +12,11 @@
 //
 // k_plain_layer is the paper's recursive mode (Appendix, Table I), one launch
 // per layer over the whole distance plane, kept as the baseline.
+#include <mutex>
+
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "mpn_internal.cuh"
 #include "wave.cuh"
@@ -152,6 +156,265 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     }
 }
 
+// ---- warp-specialised variant: a producer warp stages regions with TMA ----
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until the barrier's phase with this parity completes; false after
+// ~2 s (the caller records ERR_TIMEOUT and winds down).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity))
+        if (global_ns() - t0 > 2000000000ull) return false;
+    return true;
+}
+
+// 2-D tiled TMA load of the box at (x words, y rows) into shared memory,
+// completing on the mbarrier (byte count).
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int x, int y,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Block = NW consumer warps + 1 producer warp. The producer (lane 0 of the
+// last warp) claims tiles, loads each claimed tile's region -- free bits and
+// visit bits, then, once the visit bits have landed, this-sweep bits -- with
+// TMA into one of two shared-memory buffers, and queues the tiles a finished
+// visit reaches. The consumer warps take each buffer in turn, run the tile's
+// layers in registers (named barrier 1 only) and write back. So the next
+// tile's region arrives while the current one is computed, and claims and
+// queue pushes never stall the consumer warps. A TMA box starts at a word
+// coordinate rounded down to a multiple of 4 (16-byte rule) and is 12 words
+// wide; the region's 8 words start xoff = 0..3 words into it. Boxes outside
+// the grid (negative or past the edge) are filled with zeros.
+template <int RXW, int R, int NW>
+__global__ void __launch_bounds__((NW + 1) * 32, 2)
+    k_propagate_tma(const __grid_constant__ CUtensorMap tm_free,
+                    const __grid_constant__ CUtensorMap tm_vis,
+                    const __grid_constant__ CUtensorMap tm_nb0,
+                    const __grid_constant__ CUtensorMap tm_nb1, PropParams p) {
+    constexpr int GPW = 32 / RXW;
+    constexpr int RY = NW * GPW * R;
+    constexpr int BW = ((RXW + 3) + 3) / 4 * 4;   // box width in words
+    constexpr uint32_t BOX_BYTES = (uint32_t)(RY * BW * 4);
+    constexpr int NBAR = NW * 32;
+    static_assert(RY <= 256, "TMA box height");
+
+    __shared__ __align__(128) uint32_t sF[2][RY * BW];
+    __shared__ __align__(128) uint32_t sV[2][RY * BW];
+    __shared__ __align__(128) uint32_t sN[2][RY * BW];
+    __shared__ __align__(8) uint64_t full[2], vfull[2], done[2];
+    __shared__ int s_tile[2], s_xoff[2], s_ctile;
+    __shared__ unsigned s_fmask[2], s_done, s_maxl, s_ok;
+    __shared__ wave::VisitSmem<RXW, NW> sm;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool producer = warp == NW;
+    Ctl *ctl = p.ctl;
+    const int ntiles = p.ntx * p.nty;
+    unsigned thr_maxl = 0u;
+    unsigned long long visits = 0;   // producer lane 0
+    uint32_t q = 0;                  // slot uses so far (same sequence on both sides)
+    uint32_t pf = 0, pv = 0, pd = 0; // phase bits per buffer (bit b)
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&vfull[b], 1);
+            mbar_init(&done[b], 1);
+            s_fmask[b] = 0u;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (ld_acquire(&ctl->err) & (ERR_INVAL | ERR_OBSTACLE)) return;
+
+    wave::Visit v;
+    v.g = p.g;
+    v.dist_bits = 32;
+    v.TY = p.TY;
+    v.TXW = p.TXW;
+    v.k = p.k;
+    const size_t ntl = (size_t)ntiles;
+    for (uint32_t s = 0;; ++s) {
+        const uint32_t l0 = s * (uint32_t)p.k;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->work[(s + 2) % 3] = 0u;
+            ctl->list_len[(s + 2) % 3] = 0u;
+        }
+        v.l0 = l0;
+        v.jmax = p.k;
+        if (p.max_layers && l0 + (uint32_t)p.k > p.max_layers) v.jmax = (int)(p.max_layers - l0);
+        v.nbS = (s & 1) ? p.g.nb1 : p.g.nb0;
+        const CUtensorMap *tm_nb = (s & 1) ? &tm_nb1 : &tm_nb0;
+        const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
+        unsigned *work = &ctl->work[s % 3];
+        const uint32_t len = ld_acquire(&ctl->list_len[s % 3]);
+
+        if (producer) {
+            if (lane == 0) {
+                // stage tile t (or the end marker, t < 0) into buffer b
+                auto issue = [&](int t, int b) -> bool {
+                    s_tile[b] = t;
+                    if (t < 0) {
+                        mbar_arrive(&full[b]);
+                        return true;
+                    }
+                    const int ty = t / p.ntx, tx = t - ty * p.ntx;
+                    const int gw0 = tx * p.TXW - 1, x0 = gw0 & ~3, y0 = ty * p.TY - p.k;
+                    s_xoff[b] = gw0 - x0;
+                    mbar_arrive_tx(&vfull[b], BOX_BYTES);
+                    tma_load(sV[b], &tm_vis, x0, y0, &vfull[b]);
+                    mbar_arrive_tx(&full[b], 2 * BOX_BYTES);
+                    tma_load(sF[b], &tm_free, x0, y0, &full[b]);
+                    // this-sweep bits only after the visit bits: a bit new in
+                    // this sweep is then always masked
+                    const bool ok = mbar_wait(&vfull[b], (pv >> b) & 1u);
+                    pv ^= 1u << b;
+                    __threadfence();
+                    tma_load(sN[b], tm_nb, x0, y0, &full[b]);
+                    return ok;
+                };
+                auto claim = [&]() -> int {
+                    const uint32_t i = atomicAdd(work, 1u);
+                    return (i < len) ? (int)ld_relaxed(list + i) : -1;
+                };
+                bool ok = true;
+                int t = claim();
+                int b = (int)(q & 1u);
+                ok &= issue(t, b);
+                ++q;
+                while (t >= 0) {
+                    const int t2 = ok ? claim() : -1;
+                    const int b2 = (int)(q & 1u);
+                    ok &= issue(t2, b2);
+                    ++q;
+                    // the visit of t is done: queue what its frontier reaches
+                    if (!mbar_wait(&done[b], (pd >> b) & 1u)) ok = false;
+                    pd ^= 1u << b;
+                    const unsigned zones = s_fmask[b];
+                    s_fmask[b] = 0u;
+                    const int ty = t / p.ntx, tx = t - ty * p.ntx;
+                    if (zones) push_reached(p, ty, tx, zones, s + 1);
+                    ++visits;
+                    t = t2;
+                    b = b2;
+                }
+                if (!ok) atomicOr(&ctl->err, ERR_TIMEOUT);
+            }
+        } else {
+            for (;;) {
+                const int b = (int)(q & 1u);
+                if (threadIdx.x == 0) {
+                    int t = -1;
+                    if (mbar_wait(&full[b], (pf >> b) & 1u)) {
+                        t = s_tile[b];
+                        if (t >= 0 && !mbar_wait(&vfull[b], (pv >> b) & 1u)) t = -1;
+                    }
+                    s_ctile = t;
+                }
+                wave::bar_sync<true, NBAR>();
+                const int t = s_ctile;
+                if (t >= 0) {
+                    // every consumer acquires the staged buffer itself (both
+                    // phases are complete: thread 0 saw them, so these return
+                    // at once)
+                    mbar_wait(&full[b], (pf >> b) & 1u);
+                    mbar_wait(&vfull[b], (pv >> b) & 1u);
+                }
+                pf ^= 1u << b;
+                ++q;
+                if (t < 0) break;
+                pv ^= 1u << b;
+                // ---- the region from the staged buffer ----
+                const int w = lane % RXW;
+                const int g = warp * GPW + lane / RXW;
+                const int r0 = g * R;
+                v.ty = t / p.ntx;
+                v.tx = t - v.ty * p.ntx;
+                const int xo = s_xoff[b] + w;
+                const bool ownW = (w >= 1) && (w <= p.TXW);
+                uint32_t V[R], F[R], OWN[R];
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const int rr = r0 + i;
+                    const bool own = ownW && rr >= p.k && rr < p.k + p.TY;
+                    OWN[i] = own ? 0xffffffffu : 0u;
+                    F[i] = sF[b][rr * BW + xo];
+                    const uint32_t vv = sV[b][rr * BW + xo];
+                    V[i] = own ? vv : (vv & ~sN[b][rr * BW + xo]);
+                }
+                uint32_t fmask;
+                unsigned lastj;
+                wave::visit_core<RXW, R, NW, true>(v, sm, &ctl->err, V, F, OWN, &fmask, &lastj);
+                if (fmask) atomicOr(&s_fmask[b], fmask);
+                if (lastj) thr_maxl = max(thr_maxl, l0 + lastj);
+                wave::bar_sync<true, NBAR>();   // all zones in, all global writes issued
+                if (threadIdx.x == 0) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    mbar_arrive(&done[b]);
+                }
+            }
+        }
+
+        if (!wave::grid_barrier(ctl, gridDim.x, p.spin_limit, &s_ok)) return;
+        if (threadIdx.x == 0) {
+            unsigned d = (ld_acquire(&ctl->list_len[(s + 1) % 3]) == 0u) ||
+                         (p.max_layers && l0 + (uint32_t)p.k >= p.max_layers);
+            if (!d && s + 1 >= p.sweep_cap) {
+                atomicOr(&ctl->err, ERR_SWEEPS);
+                d = 1;
+            }
+            if (d && blockIdx.x == 0) ctl->sweeps = s + 1;
+            s_done = d;
+            s_maxl = 0u;
+        }
+        __syncthreads();
+        if (s_done) {
+            if (thr_maxl) atomicMax(&s_maxl, thr_maxl);
+            if (producer && lane == 0 && visits) atomicAdd(&ctl->visits, visits);
+            __syncthreads();
+            if (threadIdx.x == 0 && s_maxl) atomicMax(&ctl->max_layer, s_maxl);
+            return;
+        }
+    }
+}
+
 // Targets: distance 0, reached bit, frontier summary of sweep 0. A target out
 // of range or on an obstacle records an error and is skipped.
 template <typename DT>
@@ -229,12 +492,13 @@ void *variant_ptr(bool u16) {
 // rows per lane; interior = region minus k rows top and bottom and one word
 // left and right.
 constexpr VariantDesc kVariants[] = {
-    {8, 4, 8, 3},    // 128 rows x 256 cells
-    {8, 8, 8, 2},    // 256 rows x 256 cells
-    {16, 4, 8, 3},   //  64 rows x 512 cells
-    {4, 8, 8, 2},    // 512 rows x 128 cells
-    {8, 4, 4, 5},    //  64 rows x 256 cells
-    {16, 8, 8, 2},   // 128 rows x 512 cells
+    {8, 4, 8, 3, 0},    // 128 rows x 256 cells
+    {8, 8, 8, 2, 0},    // 256 rows x 256 cells
+    {16, 4, 8, 3, 0},   //  64 rows x 512 cells
+    {4, 8, 8, 2, 0},    // 512 rows x 128 cells
+    {8, 4, 4, 5, 0},    //  64 rows x 256 cells
+    {16, 8, 8, 2, 0},   // 128 rows x 512 cells
+    {8, 4, 8, 2, 1},    // 128 rows x 256 cells, TMA-staged, + producer warp (uint32 planes)
 };
 
 void *variant_fn(int v, int dist_bits) {
@@ -246,6 +510,7 @@ void *variant_fn(int v, int dist_bits) {
         case 3: return variant_ptr<4, 8, 8, 2>(u16);
         case 4: return variant_ptr<8, 4, 4, 5>(u16);
         case 5: return variant_ptr<16, 8, 8, 2>(u16);
+        case 6: return u16 ? nullptr : (void *)k_propagate_tma<8, 4, 8>;
         default: return nullptr;
     }
 }
@@ -256,21 +521,69 @@ int num_variants() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
 
 VariantDesc variant_desc(int v) { return kVariants[v]; }
 
+int variant_threads(int v) { return (kVariants[v].nwarps + kVariants[v].tma) * 32; }
+
 cudaError_t propagate_blocks_per_sm(int v, int dist_bits, int *out) {
     void *fn = variant_fn(v, dist_bits);
     if (!fn) return cudaErrorInvalidValue;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, kVariants[v].nwarps * 32, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, fn, variant_threads(v), 0);
 }
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// A bit plane (H rows x P uint32 words, P a multiple of 4) as a 2-D tensor
+// with a box of bw words x ry rows; out-of-range elements read as zero.
+cudaError_t plane_map(CUtensorMap *m, const void *base, int P, int H, int bw, int ry) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)H};
+    cuuint64_t strides[1] = {(cuuint64_t)P * 4u};
+    cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)ry};
+    cuuint32_t es[2] = {1u, 1u};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(base), dims,
+                           strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
 
 cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int blocks,
                              cudaStream_t st) {
     void *fn = variant_fn(v, dist_bits);
     if (!fn) return cudaErrorInvalidValue;
     PropParams pp = p;
-    void *args[] = {&pp};
     count_launch();
-    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kVariants[v].nwarps * 32), args, 0,
-                                       st);
+    if (!kVariants[v].tma) {
+        void *args[] = {&pp};
+        return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(variant_threads(v)), args, 0, st);
+    }
+    const VariantDesc &d = kVariants[v];
+    const int ry = d.nwarps * (32 / d.rxw) * d.r, bw = (d.rxw + 6) / 4 * 4;
+    CUtensorMap mf, mv, m0, m1;
+    cudaError_t e = plane_map(&mf, p.g.free_bits, p.g.P, p.g.H, bw, ry);
+    if (e == cudaSuccess) e = plane_map(&mv, p.g.vis, p.g.P, p.g.H, bw, ry);
+    if (e == cudaSuccess) e = plane_map(&m0, p.g.nb0, p.g.P, p.g.H, bw, ry);
+    if (e == cudaSuccess) e = plane_map(&m1, p.g.nb1, p.g.P, p.g.H, bw, ry);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&mf, &mv, &m0, &m1, &pp};
+    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(variant_threads(v)), args, 0, st);
 }
 
 cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int dist_bits,

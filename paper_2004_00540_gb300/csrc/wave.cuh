@@ -111,6 +111,29 @@ __device__ __forceinline__ uint32_t border_bits(int ri, int wi, uint32_t bits, i
     return m;
 }
 
+// Block-level OR-reduction barrier: all threads of the block (NAMED false) or
+// only the NBAR consumer threads on named barrier 1 (NAMED true), so that a
+// producer warp can run on without joining the per-layer barriers.
+template <bool NAMED, int NBAR>
+__device__ __forceinline__ int bar_or(int pred) {
+    if (!NAMED) return __syncthreads_or(pred);
+    uint32_t out;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(out) : "r"((uint32_t)pred), "n"(NBAR) : "memory");
+    return (int)out;
+}
+
+template <bool NAMED, int NBAR>
+__device__ __forceinline__ void bar_sync() {
+    if (!NAMED) {
+        __syncthreads();
+        return;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(NBAR) : "memory");
+}
+
 // One tile visit's inputs.
 struct Visit {
     GridDev g;            // planes of the grid the tile belongs to
@@ -129,52 +152,38 @@ struct VisitSmem {
     uint32_t xbot[2][G][RXW];
 };
 
-// Advance one tile by up to v.jmax layers, write the distances of the cells it
+// Advance one tile by up to v.jmax layers from its region already in
+// registers (V: visit bits as of the start of the sweep, F: free bits, OWN:
+// all-ones on this tile's interior words), write the distances of the cells it
 // reaches (a uint16 overflow sets ERR_OVERFLOW in *err), publish its new visit
-// bits (after the this-sweep bits) and return
-// the border zones of its frontier (cells reached at layer l0 + k) and, per
-// thread, the last layer at which one of this thread's cells was reached.
-// Every thread of the block calls it; it contains block barriers.
+// bits (after the this-sweep bits) and return the border zones of its frontier
+// (cells reached at layer l0 + k) and, per thread, the last layer at which one
+// of this thread's cells was reached. Every participating thread calls it; it
+// contains barriers (block-wide, or named barrier 1 when NAMED).
 //
 // Block layout: a row group is RXW consecutive lanes holding RXW consecutive
 // words of R consecutive rows (one word per lane per row, in registers).
 // Region = (NW * 32 / RXW * R) rows x RXW words; interior = rows [k, RY - k)
-// x words [1, RXW - 1). Halo words of other tiles are read as of the start of
-// the sweep: their this-sweep bits are masked out (the owner writes those
-// before its visit bits; the fences order both sides).
-template <int RXW, int R, int NW>
-__device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
-                                           uint32_t *fmask_out, unsigned *lastj_out) {
+// x words [1, RXW - 1).
+template <int RXW, int R, int NW, bool NAMED>
+__device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
+                                           uint32_t (&V)[R], const uint32_t (&F)[R],
+                                           const uint32_t (&OWN)[R], uint32_t *fmask_out,
+                                           unsigned *lastj_out) {
     constexpr int GPW = 32 / RXW;
     constexpr int G = NW * GPW;
+    constexpr int NBAR = NW * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = lane % RXW;
     const int g = warp * GPW + lane / RXW;
     const int r0 = g * R;
     const int k = v.k, TY = v.TY, TXW = v.TXW;
     const GridDev &gd = v.g;
-    const bool ownW = (w >= 1) && (w <= TXW);
-
-    // ---- load the region (tile + halo) ----
     const int y0 = v.ty * TY - k;
     const int gw = v.tx * TXW - 1 + w;
-    const bool inX = (gw >= 0) && (gw < gd.P);
-    uint32_t V[R], F[R], NB[R], OWN[R];   // OWN: all-ones on this tile's interior words
+    uint32_t NB[R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int rr = r0 + i, y = y0 + rr;
-        const bool in = inX && y >= 0 && y < gd.H;
-        const bool own = ownW && rr >= k && rr < k + TY;
-        const size_t off = (size_t)y * gd.P + gw;
-        OWN[i] = own ? 0xffffffffu : 0u;
-        F[i] = in ? __ldg(gd.free_bits + off) : 0u;
-        V[i] = in ? ld_relaxed(gd.vis + off) : 0u;
-        NB[i] = 0u;
-    }
-    __threadfence();   // visit bits before the matching this-sweep bits
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-        if (!OWN[i] && V[i]) V[i] &= ~ld_relaxed(v.nbS + (size_t)(y0 + r0 + i) * gd.P + gw);
+    for (int i = 0; i < R; ++i) NB[i] = 0u;
 
     // ---- up to k layers in registers ----
     // P[b][i]: bit b of (layer - l0 - 1) for cells first reached in this
@@ -192,7 +201,7 @@ __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &s
         const uint32_t hL = hdil<RXW>(V[R - 1]);
         sm.xtop[j & 1][g][w] = hF;
         sm.xbot[j & 1][g][w] = hL;
-        if (!__syncthreads_or(changed != 0u)) break;   // region is stable
+        if (!bar_or<NAMED, NBAR>(changed != 0u)) break;   // region is stable
         const uint32_t hUp = (g > 0) ? sm.xbot[j & 1][g - 1][w] : 0u;
         const uint32_t hDn = (g < G - 1) ? sm.xtop[j & 1][g + 1][w] : 0u;
         uint32_t h[R];
@@ -273,6 +282,42 @@ __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &s
 #pragma unroll
     for (int i = 0; i < R; ++i)
         if (NB[i]) st_relaxed(gd.vis + (size_t)(y0 + r0 + i) * gd.P + gw, V[i]);
+}
+
+// A tile visit that loads its own region from global memory (the
+// register-only kernels). Halo words of other tiles are read as of the start
+// of the sweep: their this-sweep bits are masked out (the owner writes those
+// before its visit bits; the fences order both sides).
+template <int RXW, int R, int NW>
+__device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
+                                           uint32_t *fmask_out, unsigned *lastj_out) {
+    constexpr int GPW = 32 / RXW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int w = lane % RXW;
+    const int g = warp * GPW + lane / RXW;
+    const int r0 = g * R;
+    const int k = v.k, TY = v.TY, TXW = v.TXW;
+    const GridDev &gd = v.g;
+    const bool ownW = (w >= 1) && (w <= TXW);
+    const int y0 = v.ty * TY - k;
+    const int gw = v.tx * TXW - 1 + w;
+    const bool inX = (gw >= 0) && (gw < gd.P);
+    uint32_t V[R], F[R], OWN[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int rr = r0 + i, y = y0 + rr;
+        const bool in = inX && y >= 0 && y < gd.H;
+        const bool own = ownW && rr >= k && rr < k + TY;
+        const size_t off = (size_t)y * gd.P + gw;
+        OWN[i] = own ? 0xffffffffu : 0u;
+        F[i] = in ? __ldg(gd.free_bits + off) : 0u;
+        V[i] = in ? ld_relaxed(gd.vis + off) : 0u;
+    }
+    __threadfence();   // visit bits before the matching this-sweep bits
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if (!OWN[i] && V[i]) V[i] &= ~ld_relaxed(v.nbS + (size_t)(y0 + r0 + i) * gd.P + gw);
+    visit_core<RXW, R, NW, false>(v, sm, err, V, F, OWN, fmask_out, lastj_out);
 }
 
 }  // namespace wave

@@ -186,8 +186,12 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     for (int i = 0; i < R; ++i) NB[i] = 0u;
 
     // ---- up to k layers in registers ----
-    // P[b][i]: bit b of (layer - l0 - 1) for cells first reached in this
-    // visit, so each cell's distance is written once, at the end.
+    // Activation times as a bit-sliced Gray-code counter: P[b][i] holds bit b
+    // of gray(t), t = layer - l0 - 1. Every cell not reached yet carries the
+    // same count, gray(j - 1) before layer j, so advancing all of them to
+    // gray(j) flips the single plane ctz(j) on the unreached cells (one
+    // operation per row and layer); a cell keeps its value once reached, and
+    // each cell's distance is written once, at the end of the visit.
     uint32_t P[5][R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -209,9 +213,6 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
         h[R - 1] = hL;
 #pragma unroll
         for (int i = 1; i < R - 1; ++i) h[i] = hdil<RXW>(V[i]);
-        uint32_t M[5];   // all-ones where bit b of j - 1 is set (block-uniform)
-#pragma unroll
-        for (int b = 0; b < 5; ++b) M[b] = (((j - 1) >> b) & 1) ? 0xffffffffu : 0u;
         changed = 0u;
         uint32_t own_new = 0u;
 #pragma unroll
@@ -221,23 +222,36 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
             const uint32_t nv = (up | h[i] | dn) & F[i] & ~V[i];
             V[i] |= nv;
             changed |= nv;
-            const uint32_t onv = nv & OWN[i];
-            NB[i] |= onv;
-            own_new |= onv;
-#pragma unroll
-            for (int b = 0; b < 5; ++b) P[b][i] |= onv & M[b];
+            NB[i] |= nv & OWN[i];
+            own_new |= nv & OWN[i];
         }
         if (own_new) lastj = (unsigned)j;
+        if (j < v.jmax) {   // unreached cells: gray(j - 1) -> gray(j)
+            switch (__ffs(j) - 1) {   // block-uniform
+#define MPN_FLIP(B)                                         \
+    case B:                                                 \
+        _Pragma("unroll") for (int i = 0; i < R; ++i) P[B][i] ^= ~V[i]; \
+        break;
+                MPN_FLIP(0)
+                MPN_FLIP(1)
+                MPN_FLIP(2)
+                MPN_FLIP(3)
+                MPN_FLIP(4)
+#undef MPN_FLIP
+                default: break;
+            }
+        }
     }
 
     // ---- frontier zones: cells reached at layer l0 + k ----
     uint32_t fmask = 0u;
     if (v.jmax == k) {
+        const uint32_t gk = (uint32_t)(k - 1) ^ ((uint32_t)(k - 1) >> 1);   // gray(k - 1)
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             uint32_t last = NB[i];
 #pragma unroll
-            for (int b = 0; b < 5; ++b) last &= (((k - 1) >> b) & 1) ? P[b][i] : ~P[b][i];
+            for (int b = 0; b < 5; ++b) last &= ((gk >> b) & 1) ? P[b][i] : ~P[b][i];
             fmask |= border_bits(r0 + i - k, w - 1, last, k, TY, TXW);
         }
     }
@@ -254,10 +268,13 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
             const int src = __ffs(act) - 1;
             act &= act - 1u;
             const uint32_t nb = __shfl_sync(0xffffffffu, NB[i], src);
-            uint32_t off = 0u;
+            uint32_t off = 0u;   // gray(t) of this lane's cell, then t
 #pragma unroll
             for (int b = 0; b < 5; ++b)
                 off |= ((__shfl_sync(0xffffffffu, P[b][i], src) >> lane) & 1u) << b;
+            off ^= off >> 1;
+            off ^= off >> 2;
+            off ^= off >> 4;
             const int sw = src % RXW;                 // source word column
             const int sg = warp * GPW + src / RXW;    // source row group
             const int y = y0 + sg * R + i;

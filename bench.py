@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--side", type=int, default=23170, help="grid side (default: the full workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--variant", type=int, default=-1, help="tile shape (default: autotuned)")
     ap.add_argument("--depth", type=int, default=32)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-maze batched/served part")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--plain-sample", type=int, default=32,
@@ -142,16 +143,17 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(workload: str):
+def measured_traffic(workload: str, variant: int, depth: int):
     """DRAM bytes per k_propagate launch from the committed ncu capture, or
-    None when the kernel sources changed since it was taken (or no capture
-    exists for this workload)."""
+    None when the kernel sources changed since it was taken, or the capture
+    was of another workload or tiling."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except Exception:
         return None
-    if t.get("source_sha256") != kernel_source_hash() or t.get("workload") != workload:
+    if (t.get("source_sha256") != kernel_source_hash() or t.get("workload") != workload
+            or t.get("variant") != variant or t.get("depth") != depth):
         return None
     return t.get("dram_bytes_per_launch")
 
@@ -361,8 +363,13 @@ def main():
 
     with torch.cuda.stream(stream):
         ctx = pkg.mpn_create(d_mask, H, W, pkg.MPN_DIST_U32, stream)
+    tuned = None
     if args.variant >= 0:
         pkg.mpn_set_tuning(ctx, args.variant, args.depth)
+    elif not args.no_autotune:
+        # every tile shape x depth measured on this grid (outside the timed region)
+        tv, td, tms = pkg.mpn_autotune(ctx, d_t)
+        tuned = {"variant": tv, "depth": td, "propagate_ms": tms}
     # device-resident outputs, sized once
     L = pkg.mpn_propagate(ctx, d_t)
     n = w.starts.size
@@ -417,7 +424,8 @@ def main():
     peak, peak_kind = peaks()
     achieved = units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": measured_traffic(w.name), "peak_kind": peak_kind,
+            "frac": achieved / peak, "traffic": measured_traffic(w.name, st["variant"], st["depth"]),
+            "peak_kind": peak_kind,
             "kernel": "k_propagate", "ms_per_launch": prop_avg,
             "note": "algorithmic bytes = 8.125 B per effective cell-update (mask bit + uint32 "
                     "read + write per layer); temporal blocking does each update in registers"}
@@ -468,7 +476,7 @@ def main():
         "config": {"workload": w.name, "H": H, "W": W, "targets": int(w.targets.size),
                    "starts": int(n), "layers": int(L), "path_cells": total,
                    "step": "encode + propagate + trace", "parallelism": f"replicas x{world}",
-                   "variant": st["variant"], "depth": st["depth"],
+                   "variant": st["variant"], "depth": st["depth"], "autotuned": tuned,
                    "l2": "inputs larger than L2 (uint8 mask 537 MB + uint32 distance plane 2.15 GB per step)"},
         "propagate": {"ms": prop_avg, "effective_cell_updates_per_s": units / (prop_avg * 1e-3),
                       "pct_hbm_roofline": 100 * units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / (peak * 1e9),

@@ -205,11 +205,12 @@ mpn_status configure(mpn_ctx *c, int variant, int depth) {
 }
 
 // Automatic tiling: the autotuner's choice for this size bucket if one was
-// measured, else the 128-row x 256-cell region at depth 32.
+// measured, else the 128-row x 256-cell region at depth 32 for grids up to
+// 2^22 cells (few tiles: fewer sweeps matter most) and depth 24 above.
 mpn_status auto_configure(mpn_ctx *c) {
     int v = 0, d = 32;
     if (tune_best(c->H, c->W, &v, &d) && configure(c, v, d) == MPN_OK) return MPN_OK;
-    return configure(c, 0, 32);
+    return configure(c, 0, (int64_t)c->H * c->W > (1ll << 22) ? 24 : 32);
 }
 
 mpn_status alloc_planes(mpn_ctx *c) {

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             t = s_tile;
         }
 
-        if (!wave::grid_barrier(ctl, gridDim.x, p.spin_limit, &s_ok)) return;
+        if (!wave::grid_barrier(ctl, (s + 1 - s0) * gridDim.x, p.spin_limit, &s_ok)) return;
         if (threadIdx.x == 0) {
             const unsigned done = (ld_acquire(&ctl->list_len[(s + 1) % 3]) == 0u) ||
                                   (p.round_sweeps && s + 1 - s0 >= p.round_sweeps);
@@ -235,6 +235,7 @@ __global__ void k_round_prep(BatchCtl *bc) {
     const uint32_t s = bc->next_sweep;
     bc->c.work[s % 3] = 0u;
     bc->c.err = 0u;
+    bc->c.bar_count = 0u;   // the round's barriers count from zero
 }
 
 __global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {

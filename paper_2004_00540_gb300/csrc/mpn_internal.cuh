@@ -25,8 +25,8 @@ constexpr uint32_t FB_NW = 32u, FB_NE = 64u, FB_SW = 128u, FB_SE = 256u;
 
 // Device control block of one propagation (zeroed before each run).
 struct Ctl {
-    unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned int bar_count;        // grid-barrier arrivals of this launch (monotonic)
+    unsigned int bar_gen;          // unused
     unsigned int work[3];          // claim counters of the tile lists, by sweep mod 3
     unsigned int list_len[3];      // lengths of the tile lists, by sweep mod 3
     unsigned int err;

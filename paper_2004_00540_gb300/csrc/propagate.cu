@@ -60,10 +60,11 @@ __device__ void push_reached(const PropParams &p, int ty, int tx, uint32_t zones
 template <int RXW, int R, int NW, int MINB, typename DT>
 __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     static_assert(RXW == 4 || RXW == 8 || RXW == 16 || RXW == 32, "row group width");
-    static_assert(R >= 2, "rows per lane");
+    static_assert(R >= 1, "rows per lane");
     __shared__ wave::VisitSmem<RXW, NW> sm;
     __shared__ int s_tile;
     __shared__ unsigned s_mask[2], s_done, s_maxl, s_ok;   // s_mask by visit parity
+    __shared__ uint32_t s_len;                              // length of this sweep's list
 
     const int ntiles = p.ntx * p.nty;
     Ctl *ctl = p.ctl;
@@ -82,6 +83,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     v.TXW = p.TXW;
     v.k = p.k;
     const size_t ntl = (size_t)ntiles;
+    const uint32_t G = gridDim.x;   // <= ntiles, so list + blockIdx.x is inside every list
+    if (threadIdx.x == 0) {
+        // sweep 0: entry blockIdx.x of the seeded list is this block's first tile
+        s_len = ld_acquire(&ctl->list_len[0]);
+        s_tile = (blockIdx.x < s_len) ? (int)ld_relaxed(p.lists + blockIdx.x) : -1;
+    }
+    __syncthreads();
     for (uint32_t s = 0;; ++s) {
         const uint32_t l0 = s * (uint32_t)p.k;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -95,20 +103,22 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
         v.nbS = (s & 1) ? p.g.nb1 : p.g.nb0;
         const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
         unsigned *work = &ctl->work[s % 3];
-        const uint32_t len = ld_acquire(&ctl->list_len[s % 3]);
-
-        if (threadIdx.x == 0) {
-            const uint32_t i = atomicAdd(work, 1u);
+        const uint32_t len = s_len;
+        // entries 0..G-1 go one per block without an atomic; the rest are
+        // claimed with the counter
+        int t = s_tile;
+        if (t < 0 && threadIdx.x == 0) {
+            const uint32_t i = G + atomicAdd(work, 1u);
             s_tile = (i < len) ? (int)ld_relaxed(list + i) : -1;
         }
         __syncthreads();
-        int t = s_tile;
+        t = s_tile;
         while (t >= 0) {
             // claim the next tile now; the atomic's latency hides behind this visit
             uint32_t next_i = 0;
             vq ^= 1u;
             if (threadIdx.x == 0) {
-                next_i = atomicAdd(work, 1u);
+                next_i = G + atomicAdd(work, 1u);
                 s_mask[vq] = 0u;   // last read two visits ago, before the previous visit's first barrier
             }
             v.ty = t / p.ntx;
@@ -131,12 +141,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             t = s_tile;
         }
 
-        if (!wave::grid_barrier(ctl, gridDim.x, p.spin_limit, &s_ok)) return;
+        if (!wave::grid_barrier(ctl, (s + 1) * G, p.spin_limit, &s_ok)) return;
         if (threadIdx.x == 0) {
             // decided from values no block changes before the next barrier, so
-            // every block reaches the same decision
-            unsigned done = (ld_acquire(&ctl->list_len[(s + 1) % 3]) == 0u) ||
-                            (p.max_layers && l0 + (uint32_t)p.k >= p.max_layers);
+            // every block reaches the same decision; the same read gives the
+            // next sweep's list length, and this block's first entry of it is
+            // loaded alongside
+            const uint32_t nlen = ld_acquire(&ctl->list_len[(s + 1) % 3]);
+            const int first = (int)ld_relaxed(p.lists + (size_t)((s + 1) % 3) * ntl + blockIdx.x);
+            unsigned done = (nlen == 0u) || (p.max_layers && l0 + (uint32_t)p.k >= p.max_layers);
             if (!done && s + 1 >= p.sweep_cap) {
                 atomicOr(&ctl->err, ERR_SWEEPS);
                 done = 1;
@@ -145,6 +158,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             if (done && blk_visits) atomicAdd(&ctl->visits, blk_visits);
             s_done = done;
             s_maxl = 0u;
+            s_len = nlen;
+            s_tile = (blockIdx.x < nlen) ? first : -1;
         }
         __syncthreads();
         if (s_done) {
@@ -241,6 +256,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
     __shared__ __align__(8) uint64_t full[2], vfull[2], done[2];
     __shared__ int s_tile[2], s_xoff[2], s_ctile;
     __shared__ unsigned s_fmask[2], s_done, s_maxl, s_ok;
+    __shared__ uint32_t s_len;
+    __shared__ int s_first;
     __shared__ wave::VisitSmem<RXW, NW> sm;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -260,6 +277,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
             s_fmask[b] = 0u;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const uint32_t G = gridDim.x;
+    if (threadIdx.x == 0) {
+        s_len = ld_acquire(&ctl->list_len[0]);
+        s_first = (blockIdx.x < s_len) ? (int)ld_relaxed(p.lists + blockIdx.x) : -1;
     }
     __syncthreads();
     if (ld_acquire(&ctl->err) & (ERR_INVAL | ERR_OBSTACLE)) return;
@@ -284,7 +306,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
         const CUtensorMap *tm_nb = (s & 1) ? &tm_nb1 : &tm_nb0;
         const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
         unsigned *work = &ctl->work[s % 3];
-        const uint32_t len = ld_acquire(&ctl->list_len[s % 3]);
+        const uint32_t len = s_len;
+        const int first = s_first;
 
         if (producer) {
             if (lane == 0) {
@@ -311,11 +334,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
                     return ok;
                 };
                 auto claim = [&]() -> int {
-                    const uint32_t i = atomicAdd(work, 1u);
+                    const uint32_t i = G + atomicAdd(work, 1u);
                     return (i < len) ? (int)ld_relaxed(list + i) : -1;
                 };
                 bool ok = true;
-                int t = claim();
+                int t = first >= 0 ? first : claim();
                 int b = (int)(q & 1u);
                 ok &= issue(t, b);
                 ++q;
@@ -392,10 +415,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
             }
         }
 
-        if (!wave::grid_barrier(ctl, gridDim.x, p.spin_limit, &s_ok)) return;
+        if (!wave::grid_barrier(ctl, (s + 1) * G, p.spin_limit, &s_ok)) return;
         if (threadIdx.x == 0) {
-            unsigned d = (ld_acquire(&ctl->list_len[(s + 1) % 3]) == 0u) ||
-                         (p.max_layers && l0 + (uint32_t)p.k >= p.max_layers);
+            const uint32_t nlen = ld_acquire(&ctl->list_len[(s + 1) % 3]);
+            const int f = (int)ld_relaxed(p.lists + (size_t)((s + 1) % 3) * ntl + blockIdx.x);
+            unsigned d = (nlen == 0u) || (p.max_layers && l0 + (uint32_t)p.k >= p.max_layers);
             if (!d && s + 1 >= p.sweep_cap) {
                 atomicOr(&ctl->err, ERR_SWEEPS);
                 d = 1;
@@ -403,6 +427,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
             if (d && blockIdx.x == 0) ctl->sweeps = s + 1;
             s_done = d;
             s_maxl = 0u;
+            s_len = nlen;
+            s_first = (blockIdx.x < nlen) ? f : -1;
         }
         __syncthreads();
         if (s_done) {
@@ -499,6 +525,8 @@ constexpr VariantDesc kVariants[] = {
     {8, 4, 4, 5, 0},    //  64 rows x 256 cells
     {16, 8, 8, 2, 0},   // 128 rows x 512 cells
     {8, 4, 8, 2, 1},    // 128 rows x 256 cells, TMA-staged, + producer warp (uint32 planes)
+    {8, 2, 16, 2, 0},   // 128 rows x 256 cells, 2 rows per lane (shorter per-layer chains)
+    {8, 1, 32, 1, 0},   // 128 rows x 256 cells, 1 row per lane, 1024 threads
 };
 
 void *variant_fn(int v, int dist_bits) {
@@ -511,6 +539,8 @@ void *variant_fn(int v, int dist_bits) {
         case 4: return variant_ptr<8, 4, 4, 5>(u16);
         case 5: return variant_ptr<16, 8, 8, 2>(u16);
         case 6: return u16 ? nullptr : (void *)k_propagate_tma<8, 4, 8>;
+        case 7: return variant_ptr<8, 2, 16, 2>(u16);
+        case 8: return variant_ptr<8, 1, 32, 1>(u16);
         default: return nullptr;
     }
 }

@@ -37,35 +37,34 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
-// Grid-wide barrier for a co-resident (cooperative) grid. The wait is bounded:
-// past spin_limit polls the block records ERR_TIMEOUT and returns false; a
-// block that sees ERR_TIMEOUT already recorded also stops waiting, so one
-// expired wait ends every block instead of starting a new wait in each.
-__device__ __forceinline__ bool grid_barrier(Ctl *c, unsigned nblocks, unsigned spin_limit,
+// Grid-wide barrier for a co-resident (cooperative) grid on a monotonic
+// arrival counter: the n-th barrier of a launch completes when the counter
+// reaches target = n * blocks, so no block resets or bumps anything after
+// arriving. The wait is bounded: past spin_limit polls the block records
+// ERR_TIMEOUT and returns false; a block that sees ERR_TIMEOUT already recorded
+// also stops waiting, so one expired wait ends every block instead of starting
+// a new wait in each.
+__device__ __forceinline__ bool grid_barrier(Ctl *c, unsigned target, unsigned spin_limit,
                                              unsigned *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned ok = 1;
-        const unsigned gen = ld_acquire(&c->bar_gen);
         __threadfence();
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
+        const unsigned arrived = atomicAdd(&c->bar_count, 1u) + 1u;
+        if (arrived < target) {
             unsigned spins = 0;
-            while (ld_acquire(&c->bar_gen) == gen) {
-                if (ld_acquire(&c->err) & ERR_TIMEOUT) {   // another block gave up
+            while (ld_acquire(&c->bar_count) < target) {
+                ++spins;
+                if ((spins & 63u) == 0u && (ld_acquire(&c->err) & ERR_TIMEOUT)) {   // another block gave up
                     ok = 0;
                     break;
                 }
-                if (++spins > spin_limit) {
+                if (spins > spin_limit) {
                     atomicOr(&c->err, ERR_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(100);
+                if (spins > 8) __nanosleep(32);
             }
         }
         __threadfence();

@@ -213,7 +213,6 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
 #pragma unroll
         for (int i = 1; i < R - 1; ++i) h[i] = hdil<RXW>(V[i]);
         changed = 0u;
-        uint32_t own_new = 0u;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const uint32_t up = (i > 0) ? h[i - 1] : hUp;
@@ -222,9 +221,7 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
             V[i] |= nv;
             changed |= nv;
             NB[i] |= nv & OWN[i];
-            own_new |= nv & OWN[i];
         }
-        if (own_new) lastj = (unsigned)j;
         if (j < v.jmax) {   // unreached cells: gray(j - 1) -> gray(j)
             switch (__ffs(j) - 1) {   // block-uniform
 #define MPN_FLIP(B)                                         \
@@ -240,6 +237,28 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
                 default: break;
             }
         }
+    }
+
+    // ---- the last layer at which one of this thread's cells was reached ----
+    // (a bit-sliced maximum of t over the reached cells, from the planes
+    // turned from Gray code into binary, most significant bit first)
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        if (!NB[i]) continue;
+        uint32_t B[5];
+        B[4] = P[4][i];
+#pragma unroll
+        for (int b = 3; b >= 0; --b) B[b] = P[b][i] ^ B[b + 1];
+        uint32_t cand = NB[i], m = 0u;
+#pragma unroll
+        for (int b = 4; b >= 0; --b) {
+            const uint32_t hit = cand & B[b];
+            if (hit) {
+                m |= 1u << b;
+                cand = hit;
+            }
+        }
+        lastj = max(lastj, m + 1u);
     }
 
     // ---- frontier zones: cells reached at layer l0 + k ----

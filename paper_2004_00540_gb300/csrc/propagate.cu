@@ -386,7 +386,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
                 pv ^= 1u << b;
                 // ---- the region from the staged buffer ----
                 const int w = lane % RXW;
-                const int g = warp * GPW + lane / RXW;
+                const int g = wave::row_group<RXW, NW>(warp, lane);
                 const int r0 = g * R;
                 v.ty = t / p.ntx;
                 v.tx = t - v.ty * p.ntx;

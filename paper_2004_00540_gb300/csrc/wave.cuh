@@ -144,11 +144,29 @@ struct Visit {
     int jmax;             // layers to run (k, or fewer at a layer cap)
 };
 
+// Row group of a lane. The NW * 32 / RXW row groups of a region (R rows
+// each, top to bottom) are dealt to the warps round-robin: group g sits in warp
+// g % NW, lane group g / NW. So every warp holds rows of the top halo, the
+// interior and the bottom halo alike, and the per-warp distance write-out at
+// the end of a visit (one store per reached word) is balanced.
+template <int RXW, int NW>
+__device__ __forceinline__ int row_group(int warp, int lane) {
+    return (lane / RXW) * NW + warp;
+}
+
+// Shared-memory slot of word w of row group g in the halo exchange: the slots
+// of a warp are 32 consecutive words, so the writes and the reads of the
+// neighbouring groups' rows are free of bank conflicts.
+template <int RXW, int NW>
+__device__ __forceinline__ int xslot(int g, int w) {
+    return (g % NW) * 32 + (g / NW) * RXW + w;
+}
+
 template <int RXW, int NW>
 struct VisitSmem {
     static constexpr int G = NW * (32 / RXW);
-    uint32_t xtop[2][G][RXW];
-    uint32_t xbot[2][G][RXW];
+    uint32_t xtop[2][NW * 32];   // per layer parity: top row of each group, dilated along the row
+    uint32_t xbot[2][NW * 32];   // bottom row
 };
 
 // Advance one tile by up to v.jmax layers from its region already in
@@ -174,12 +192,15 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     constexpr int NBAR = NW * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = lane % RXW;
-    const int g = warp * GPW + lane / RXW;
+    const int g = row_group<RXW, NW>(warp, lane);
     const int r0 = g * R;
     const int k = v.k, TY = v.TY, TXW = v.TXW;
     const GridDev &gd = v.g;
     const int y0 = v.ty * TY - k;
     const int gw = v.tx * TXW - 1 + w;
+    const int slot = warp * 32 + lane;   // == xslot(g, w)
+    const int slot_up = g > 0 ? xslot<RXW, NW>(g - 1, w) : 0;
+    const int slot_dn = g < G - 1 ? xslot<RXW, NW>(g + 1, w) : 0;
     uint32_t NB[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) NB[i] = 0u;
@@ -202,11 +223,11 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     for (int j = 1; j <= v.jmax; ++j) {
         const uint32_t hF = hdil<RXW>(V[0]);
         const uint32_t hL = hdil<RXW>(V[R - 1]);
-        sm.xtop[j & 1][g][w] = hF;
-        sm.xbot[j & 1][g][w] = hL;
+        sm.xtop[j & 1][slot] = hF;
+        sm.xbot[j & 1][slot] = hL;
         if (!bar_or<NAMED, NBAR>(changed != 0u)) break;   // region is stable
-        const uint32_t hUp = (g > 0) ? sm.xbot[j & 1][g - 1][w] : 0u;
-        const uint32_t hDn = (g < G - 1) ? sm.xtop[j & 1][g + 1][w] : 0u;
+        const uint32_t hUp = (g > 0) ? sm.xbot[j & 1][slot_up] : 0u;
+        const uint32_t hDn = (g < G - 1) ? sm.xtop[j & 1][slot_dn] : 0u;
         uint32_t h[R];
         h[0] = hF;
         h[R - 1] = hL;
@@ -294,7 +315,7 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
             off ^= off >> 2;
             off ^= off >> 4;
             const int sw = src % RXW;                 // source word column
-            const int sg = warp * GPW + src / RXW;    // source row group
+            const int sg = row_group<RXW, NW>(warp, src);   // source row group
             const int y = y0 + sg * R + i;
             const size_t cell = (size_t)y * gd.W + (size_t)(v.tx * TXW - 1 + sw) * 32 + lane;
             if ((nb >> lane) & 1u) {
@@ -326,10 +347,9 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
 template <int RXW, int R, int NW>
 __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
                                            uint32_t *fmask_out, unsigned *lastj_out) {
-    constexpr int GPW = 32 / RXW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = lane % RXW;
-    const int g = warp * GPW + lane / RXW;
+    const int g = row_group<RXW, NW>(warp, lane);
     const int r0 = g * R;
     const int k = v.k, TY = v.TY, TXW = v.TXW;
     const GridDev &gd = v.g;

@@ -55,8 +55,23 @@ __device__ void push_reached(const PropParams &p, int ty, int tx, uint32_t zones
     if (zones & FB_SE) push_tile(p, ty + 1, tx + 1, s);
 }
 
+// The tile that frontier cells in border zone z (one FB_* bit) of tile
+// (ty, tx) can reach, or -1 past the grid's edge.
+__device__ __forceinline__ int zone_tile(const PropParams &p, int ty, int tx, uint32_t z) {
+    if (z & (FB_N | FB_NW | FB_NE)) --ty;
+    if (z & (FB_S | FB_SW | FB_SE)) ++ty;
+    if (z & (FB_W | FB_NW | FB_SW)) --tx;
+    if (z & (FB_E | FB_NE | FB_SE)) ++tx;
+    if (ty < 0 || tx < 0 || ty >= p.nty || tx >= p.ntx) return -1;
+    return ty * p.ntx + tx;
+}
+
 // Persistent temporally blocked propagation over one grid (tile shapes: see
-// wave::visit_tile).
+// wave::visit_tile). A visit's queue pushes are split across the next visit:
+// lanes 0..8 (one border zone each) issue the stamp's atomicMax after the
+// visit, and append the tile to the list once the next visit's layers are
+// done, so neither atomic's round trip stands between two visits; the last
+// visit of a sweep finishes its pushes before the grid barrier.
 template <int RXW, int R, int NW, int MINB, typename DT>
 __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     static_assert(RXW == 4 || RXW == 8 || RXW == 16 || RXW == 32, "row group width");
@@ -113,6 +128,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
         }
         __syncthreads();
         t = s_tile;
+        const uint32_t stamp = s + 2u;             // queued for sweep s + 1
+        const uint32_t slot1 = (s + 1u) % 3u;
+        int pend_t = -1;                           // lanes 0..8: tile of a push in flight
+        uint32_t pend_old = 0u;                    // its stamp before the atomicMax
         while (t >= 0) {
             // claim the next tile now; the atomic's latency hides behind this visit
             uint32_t next_i = 0;
@@ -126,6 +145,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             uint32_t fmask;
             unsigned lastj;
             wave::visit_tile<RXW, R, NW>(v, sm, &ctl->err, &fmask, &lastj);
+            uint32_t pend_i = 0u;
+            const bool pend_new = pend_t >= 0 && pend_old < stamp;   // previous visit's push
+            if (pend_new) pend_i = atomicAdd(&ctl->list_len[slot1], 1u);
             if (fmask) atomicOr(&s_mask[vq], fmask);
             if (lastj) thr_maxl = max(thr_maxl, l0 + lastj);
             if (threadIdx.x == 0) {
@@ -134,11 +156,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             }
             __syncthreads();
             if (threadIdx.x < 9) {
-                // lanes 0..8 each queue one of the tiles the frontier reaches
+                if (pend_new) p.lists[(size_t)slot1 * ntl + pend_i] = (uint32_t)pend_t;
+                // this visit's push for border zone threadIdx.x: stamp now, append later
                 const uint32_t zone = 1u << threadIdx.x;
-                if (s_mask[vq] & zone) push_reached(p, v.ty, v.tx, zone, s + 1);
+                pend_t = (s_mask[vq] & zone) ? zone_tile(p, v.ty, v.tx, zone) : -1;
+                if (pend_t >= 0) pend_old = atomicMax(p.queued + pend_t, stamp);
             }
             t = s_tile;
+        }
+        if (pend_t >= 0 && pend_old < stamp) {   // the sweep's last visit
+            const uint32_t i = atomicAdd(&ctl->list_len[slot1], 1u);
+            p.lists[(size_t)slot1 * ntl + i] = (uint32_t)pend_t;
         }
 
         if (!wave::grid_barrier(ctl, (s + 1) * G, p.spin_limit, &s_ok)) return;

@@ -80,6 +80,17 @@ __device__ __forceinline__ void push_tile_b(const BatchParams &p, const MazeDesc
     }
 }
 
+// The tile of grid d that frontier cells in border zone z (one FB_* bit) of
+// its tile (ty, tx) can reach, as a global tile id, or -1 past the grid's edge.
+__device__ __forceinline__ int64_t zone_tile_b(const MazeDesc &d, int ty, int tx, uint32_t z) {
+    if (z & (FB_N | FB_NW | FB_NE)) --ty;
+    if (z & (FB_S | FB_SW | FB_SE)) ++ty;
+    if (z & (FB_W | FB_NW | FB_SW)) --tx;
+    if (z & (FB_E | FB_NE | FB_SE)) ++tx;
+    if (ty < 0 || tx < 0 || ty >= d.nty || tx >= d.ntx) return -1;
+    return (int64_t)d.tile_base + ty * d.ntx + tx;
+}
+
 __device__ void push_zone_b(const BatchParams &p, const MazeDesc &d, uint32_t slot, int ty, int tx,
                             uint32_t zone, uint32_t s) {
     if (zone & FB_ANY) push_tile_b(p, d, slot, ty, tx, s);
@@ -121,6 +132,10 @@ __global__ void k_batch_seed(BatchParams p, const SeedJob *jobs) {
     }
 }
 
+// The round's sweeps over every admitted grid's queued tiles. As in the
+// single-grid kernel, entries 0 .. blocks - 1 of a sweep's list go one per
+// block without an atomic, and a visit's queue pushes are split across the
+// next visit (stamp after the visit, append after the next visit's layers).
 template <int RXW, int R, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p) {
     __shared__ wave::VisitSmem<RXW, NW> sm;
@@ -139,17 +154,19 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
         const uint32_t *list = p.lists + (size_t)(s % 3) * p.max_tiles;
         unsigned *work = &ctl->work[s % 3];
         const uint32_t len = ld_acquire(&ctl->list_len[s % 3]);
-        if (threadIdx.x == 0) {
-            const uint32_t i = atomicAdd(work, 1u);
-            s_tile = (i < len) ? (int)ld_relaxed(list + i) : -1;
-        }
+        const uint32_t G = gridDim.x;
+        if (threadIdx.x == 0) s_tile = (blockIdx.x < len) ? (int)ld_relaxed(list + blockIdx.x) : -1;
         __syncthreads();
         int t = s_tile;
+        const uint32_t stamp = s + 2u;            // queued for sweep s + 1
+        const uint32_t sl1 = (s + 1u) % 3u;
+        int64_t pend_gt = -1;                     // lanes 0..8: global tile of a push in flight
+        uint32_t pend_old = 0u, pend_slot = 0u;   // its stamp before the atomicMax, its grid
         while (t >= 0) {
             uint32_t next_i = 0;
             vq ^= 1u;
             if (threadIdx.x == 0) {
-                next_i = atomicAdd(work, 1u);
+                next_i = G + atomicAdd(work, 1u);
                 s_mask[vq] = 0u;
                 s_lastj[vq] = 0u;
             }
@@ -176,6 +193,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             unsigned lastj = 0u;
             if (valid) wave::visit_tile<RXW, R, NW>(v, sm, &p.descs[slot].err, &fmask, &lastj);
             if (maxl && v.l0 + (uint32_t)v.k >= maxl) fmask = 0u;   // fixed depth reached
+            uint32_t pend_i = 0u;
+            const bool pend_new = pend_gt >= 0 && pend_old < stamp;   // previous visit's push
+            if (pend_new) pend_i = atomicAdd(&ctl->list_len[sl1], 1u);
             if (fmask) atomicOr(&s_mask[vq], fmask);
             if (lastj) atomicMax(&s_lastj[vq], lastj);
             if (threadIdx.x == 0) {
@@ -184,12 +204,26 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             }
             __syncthreads();
             if (threadIdx.x < 9) {
+                if (pend_new) {
+                    p.lists[(size_t)sl1 * p.max_tiles + pend_i] = (uint32_t)pend_gt;
+                    atomicMax(&p.descs[pend_slot].last_push, stamp);
+                }
+                // this visit's push for border zone threadIdx.x: stamp now, append later
                 const uint32_t zone = 1u << threadIdx.x;
-                if (s_mask[vq] & zone) push_zone_b(p, dref, slot, v.ty, v.tx, zone, s + 1);
+                pend_gt = (s_mask[vq] & zone) ? zone_tile_b(dref, v.ty, v.tx, zone) : -1;
+                if (pend_gt >= 0) {
+                    pend_slot = slot;
+                    pend_old = atomicMax(p.queued + pend_gt, stamp);
+                }
                 if (threadIdx.x == 0 && s_lastj[vq])
                     atomicMax(&p.descs[slot].maxl, v.l0 + s_lastj[vq]);
             }
             t = s_tile;
+        }
+        if (pend_gt >= 0 && pend_old < stamp) {   // the sweep's last visit
+            const uint32_t i = atomicAdd(&ctl->list_len[sl1], 1u);
+            p.lists[(size_t)sl1 * p.max_tiles + i] = (uint32_t)pend_gt;
+            atomicMax(&p.descs[pend_slot].last_push, stamp);
         }
 
         if (!wave::grid_barrier(ctl, (s + 1 - s0) * gridDim.x, p.spin_limit, &s_ok)) return;

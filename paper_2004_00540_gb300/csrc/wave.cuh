@@ -201,9 +201,9 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     const int slot = warp * 32 + lane;   // == xslot(g, w)
     const int slot_up = g > 0 ? xslot<RXW, NW>(g - 1, w) : 0;
     const int slot_dn = g < G - 1 ? xslot<RXW, NW>(g + 1, w) : 0;
-    uint32_t NB[R];
+    uint32_t V0[R];   // visit bits at the start of the visit
 #pragma unroll
-    for (int i = 0; i < R; ++i) NB[i] = 0u;
+    for (int i = 0; i < R; ++i) V0[i] = V[i];
 
     // ---- up to k layers in registers ----
     // Activation times as a bit-sliced Gray-code counter: P[b][i] holds bit b
@@ -218,30 +218,30 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
 #pragma unroll
         for (int b = 0; b < 5; ++b) P[b][i] = 0u;
     }
+    // Per layer: every row dilated along the row first (the shuffles of the
+    // inner rows overlap the wait at the barrier), the group's top and bottom
+    // rows exchanged through shared memory, then a row's new bits are the
+    // vertical OR of three dilated rows within the free cells. The bits a
+    // visit reaches are recovered at the end against V0.
     uint32_t changed = 1u;
     unsigned lastj = 0u;
     for (int j = 1; j <= v.jmax; ++j) {
-        const uint32_t hF = hdil<RXW>(V[0]);
-        const uint32_t hL = hdil<RXW>(V[R - 1]);
-        sm.xtop[j & 1][slot] = hF;
-        sm.xbot[j & 1][slot] = hL;
+        uint32_t h[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) h[i] = hdil<RXW>(V[i]);
+        sm.xtop[j & 1][slot] = h[0];
+        sm.xbot[j & 1][slot] = h[R - 1];
         if (!bar_or<NAMED, NBAR>(changed != 0u)) break;   // region is stable
         const uint32_t hUp = (g > 0) ? sm.xbot[j & 1][slot_up] : 0u;
         const uint32_t hDn = (g < G - 1) ? sm.xtop[j & 1][slot_dn] : 0u;
-        uint32_t h[R];
-        h[0] = hF;
-        h[R - 1] = hL;
-#pragma unroll
-        for (int i = 1; i < R - 1; ++i) h[i] = hdil<RXW>(V[i]);
         changed = 0u;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const uint32_t up = (i > 0) ? h[i - 1] : hUp;
             const uint32_t dn = (i < R - 1) ? h[i + 1] : hDn;
-            const uint32_t nv = (up | h[i] | dn) & F[i] & ~V[i];
-            V[i] |= nv;
-            changed |= nv;
-            NB[i] |= nv & OWN[i];
+            const uint32_t vn = V[i] | ((up | h[i] | dn) & F[i]);
+            changed |= vn ^ V[i];
+            V[i] = vn;
         }
         if (j < v.jmax) {   // unreached cells: gray(j - 1) -> gray(j)
             switch (__ffs(j) - 1) {   // block-uniform
@@ -259,6 +259,11 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
             }
         }
     }
+
+    // cells of this tile's interior first reached in this visit
+    uint32_t NB[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) NB[i] = (V[i] ^ V0[i]) & OWN[i];
 
     // ---- the last layer at which one of this thread's cells was reached ----
     // (a bit-sliced maximum of t over the reached cells, from the planes

@@ -225,15 +225,16 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     // visit reaches are recovered at the end against V0.
     uint32_t changed = 1u;
     unsigned lastj = 0u;
-    for (int j = 1; j <= v.jmax; ++j) {
+    // one layer with the exchange slots of its parity; false: region stable
+    auto layer = [&](uint32_t *xt, uint32_t *xb) -> bool {
         uint32_t h[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) h[i] = hdil<RXW>(V[i]);
-        sm.xtop[j & 1][slot] = h[0];
-        sm.xbot[j & 1][slot] = h[R - 1];
-        if (!bar_or<NAMED, NBAR>(changed != 0u)) break;   // region is stable
-        const uint32_t hUp = (g > 0) ? sm.xbot[j & 1][slot_up] : 0u;
-        const uint32_t hDn = (g < G - 1) ? sm.xtop[j & 1][slot_dn] : 0u;
+        xt[slot] = h[0];
+        xb[slot] = h[R - 1];
+        if (!bar_or<NAMED, NBAR>(changed != 0u)) return false;
+        const uint32_t hUp = (g > 0) ? xb[slot_up] : 0u;
+        const uint32_t hDn = (g < G - 1) ? xt[slot_dn] : 0u;
         changed = 0u;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
@@ -243,22 +244,24 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
             changed |= vn ^ V[i];
             V[i] = vn;
         }
-        if (j < v.jmax) {   // unreached cells: gray(j - 1) -> gray(j)
-            switch (__ffs(j) - 1) {   // block-uniform
-#define MPN_FLIP(B)                                         \
-    case B:                                                 \
-        _Pragma("unroll") for (int i = 0; i < R; ++i) P[B][i] ^= ~V[i]; \
-        break;
-                MPN_FLIP(0)
-                MPN_FLIP(1)
-                MPN_FLIP(2)
-                MPN_FLIP(3)
-                MPN_FLIP(4)
-#undef MPN_FLIP
-                default: break;
-            }
+        return true;
+    };
+    // unreached cells: gray(j - 1) -> gray(j), plane ctz(j)
+#define MPN_FLIP(B) _Pragma("unroll") for (int i = 0; i < R; ++i) P[B][i] ^= ~V[i]
+    for (int j = 1; j <= v.jmax; j += 2) {   // j odd: ctz(j) = 0
+        if (!layer(sm.xtop[1], sm.xbot[1])) break;
+        if (j == v.jmax) break;
+        MPN_FLIP(0);
+        if (!layer(sm.xtop[0], sm.xbot[0])) break;
+        if (j + 1 == v.jmax) break;
+        switch (__ffs(j + 1) - 1) {   // 1..4 (j + 1 < 32), block-uniform
+            case 1: MPN_FLIP(1); break;
+            case 2: MPN_FLIP(2); break;
+            case 3: MPN_FLIP(3); break;
+            default: MPN_FLIP(4); break;
         }
     }
+#undef MPN_FLIP
 
     // cells of this tile's interior first reached in this visit
     uint32_t NB[R];

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
     unsigned vq = 0u;
     unsigned long long blk_visits = 0;
     const uint32_t s0 = ld_acquire(&p.bc->next_sweep);
+    sm.zero_pad();   // (the first barrier below publishes it)
 
     for (uint32_t s = s0;; ++s) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {

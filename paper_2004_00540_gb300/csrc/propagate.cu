@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     unsigned long long blk_visits = 0;   // thread 0: tile visits of this block
     unsigned vq = 0u;                    // visit parity (block-uniform)
 
+    sm.zero_pad();   // (the first barrier below publishes it)
     // the seeding step rejected the targets (nothing in this kernel sets these
     // bits, so every block takes the same branch)
     if (ld_acquire(&ctl->err) & (ERR_INVAL | ERR_OBSTACLE)) return;
@@ -297,6 +298,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
     uint32_t q = 0;                  // slot uses so far (same sequence on both sides)
     uint32_t pf = 0, pv = 0, pd = 0; // phase bits per buffer (bit b)
 
+    sm.zero_pad();
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&full[b], 1);

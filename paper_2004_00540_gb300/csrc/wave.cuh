@@ -16,6 +16,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mpn_internal.cuh"
 
 namespace mpn {
@@ -165,8 +167,11 @@ __device__ __forceinline__ int xslot(int g, int w) {
 template <int RXW, int NW>
 struct VisitSmem {
     static constexpr int G = NW * (32 / RXW);
-    uint32_t xtop[2][NW * 32];   // per layer parity: top row of each group, dilated along the row
-    uint32_t xbot[2][NW * 32];   // bottom row
+    uint32_t xtop[2][NW * 32 + 1];   // per layer parity: top row of each group, dilated along the row
+    uint32_t xbot[2][NW * 32 + 1];   // bottom row; [NW * 32]: zero, the region's outer neighbours
+    __device__ __forceinline__ void zero_pad() {
+        if (threadIdx.x < 4) (threadIdx.x < 2 ? xtop : xbot)[threadIdx.x & 1][NW * 32] = 0u;
+    }
 };
 
 // Advance one tile by up to v.jmax layers from its region already in
@@ -199,8 +204,8 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     const int y0 = v.ty * TY - k;
     const int gw = v.tx * TXW - 1 + w;
     const int slot = warp * 32 + lane;   // == xslot(g, w)
-    const int slot_up = g > 0 ? xslot<RXW, NW>(g - 1, w) : 0;
-    const int slot_dn = g < G - 1 ? xslot<RXW, NW>(g + 1, w) : 0;
+    const int slot_up = g > 0 ? xslot<RXW, NW>(g - 1, w) : NW * 32;
+    const int slot_dn = g < G - 1 ? xslot<RXW, NW>(g + 1, w) : NW * 32;
     uint32_t V0[R];   // visit bits at the start of the visit
 #pragma unroll
     for (int i = 0; i < R; ++i) V0[i] = V[i];
@@ -222,26 +227,34 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     // inner rows overlap the wait at the barrier), the group's top and bottom
     // rows exchanged through shared memory, then a row's new bits are the
     // vertical OR of three dilated rows within the free cells. The bits a
-    // visit reaches are recovered at the end against V0.
+    // visit reaches are recovered at the end against V0. Layers run in pairs:
+    // an even layer records whether it changed anything and the next odd
+    // layer's barrier ORs that over the block and ends the visit if nothing
+    // did (a stable region costs at most one extra layer); the row groups at
+    // the region's top and bottom edge read a zero exchange slot.
     uint32_t changed = 1u;
     unsigned lastj = 0u;
     // one layer with the exchange slots of its parity; false: region stable
-    auto layer = [&](uint32_t *xt, uint32_t *xb) -> bool {
+    auto layer = [&](uint32_t *xt, uint32_t *xb, auto odd) -> bool {
         uint32_t h[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) h[i] = hdil<RXW>(V[i]);
         xt[slot] = h[0];
         xb[slot] = h[R - 1];
-        if (!bar_or<NAMED, NBAR>(changed != 0u)) return false;
-        const uint32_t hUp = (g > 0) ? xb[slot_up] : 0u;
-        const uint32_t hDn = (g < G - 1) ? xt[slot_dn] : 0u;
-        changed = 0u;
+        if (decltype(odd)::value) {
+            if (!bar_or<NAMED, NBAR>(changed != 0u)) return false;
+        } else {
+            bar_sync<NAMED, NBAR>();
+        }
+        const uint32_t hUp = xb[slot_up];
+        const uint32_t hDn = xt[slot_dn];
+        if (!decltype(odd)::value) changed = 0u;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const uint32_t up = (i > 0) ? h[i - 1] : hUp;
             const uint32_t dn = (i < R - 1) ? h[i + 1] : hDn;
             const uint32_t vn = V[i] | ((up | h[i] | dn) & F[i]);
-            changed |= vn ^ V[i];
+            if (!decltype(odd)::value) changed |= vn ^ V[i];
             V[i] = vn;
         }
         return true;
@@ -249,10 +262,10 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     // unreached cells: gray(j - 1) -> gray(j), plane ctz(j)
 #define MPN_FLIP(B) _Pragma("unroll") for (int i = 0; i < R; ++i) P[B][i] ^= ~V[i]
     for (int j = 1; j <= v.jmax; j += 2) {   // j odd: ctz(j) = 0
-        if (!layer(sm.xtop[1], sm.xbot[1])) break;
+        if (!layer(sm.xtop[1], sm.xbot[1], std::true_type())) break;
         if (j == v.jmax) break;
         MPN_FLIP(0);
-        if (!layer(sm.xtop[0], sm.xbot[0])) break;
+        if (!layer(sm.xtop[0], sm.xbot[0], std::false_type())) break;
         if (j + 1 == v.jmax) break;
         switch (__ffs(j + 1) - 1) {   // 1..4 (j + 1 < 32), block-uniform
             case 1: MPN_FLIP(1); break;

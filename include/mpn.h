@@ -343,7 +343,7 @@ void mpn_batch_destroy(mpn_batch *b);
  * MPN_EOBSTACLE for one on an obstacle).
  *
  * Limit: H <= 2048 and W <= 2048; larger grids return MPN_EINVAL. The scratch
- * (bit planes, tile queue, control block; about 2.1 MB) is one fixed device
+ * (bit planes, tile queue, control block; about 2.6 MB) is one fixed device
  * array that every GPU loading this library holds until the process exits.
  * Calls never call cudaMalloc/cudaFree or any allocating routine. The first
  * call on each device looks up that array's device address

@@ -139,7 +139,7 @@ struct mpn_ctx {
     int device = 0, sm_count = 0;
     cudaStream_t stream = nullptr;
 
-    DevBuf free_bits, vis, nb0, nb1, dist, ctl, tiles, mask_stage;
+    DevBuf free_bits, state, dist, ctl, tiles, mask_stage;
     DevBuf targets, starts, offsets, status, cells, activity;
 
     int variant = 0, depth = 32;
@@ -158,9 +158,7 @@ struct mpn_ctx {
     GridDev grid() const {
         GridDev g;
         g.free_bits = (const uint32_t *)free_bits.p;
-        g.vis = (uint32_t *)vis.p;
-        g.nb0 = (uint32_t *)nb0.p;
-        g.nb1 = (uint32_t *)nb1.p;
+        g.state = (uint32_t *)state.p;
         g.dist = dist.p;
         g.H = H;
         g.W = W;
@@ -216,9 +214,7 @@ mpn_status auto_configure(mpn_ctx *c) {
 mpn_status alloc_planes(mpn_ctx *c) {
     const size_t pw = c->plane_words() * sizeof(uint32_t);
     MPN_TRY(c->free_bits.ensure(pw));
-    MPN_TRY(c->vis.ensure(pw));
-    MPN_TRY(c->nb0.ensure(pw));
-    MPN_TRY(c->nb1.ensure(pw));
+    MPN_TRY(c->state.ensure(4 * pw));
     MPN_TRY(c->dist.ensure(c->dist_bytes()));
     MPN_TRY(c->ctl.ensure(sizeof(Ctl)));
     for (auto &e : c->ev) MPN_TRY(cudaEventCreate(&e));
@@ -318,7 +314,7 @@ mpn_status begin_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n,
     st = stage_u32(c, c->targets, targets, n, dt);
     if (st != MPN_OK) return st;
     MPN_TRY(cudaMemsetAsync(c->dist.p, 0xff, c->dist_bytes(), c->stream));
-    MPN_TRY(cudaMemsetAsync(c->vis.p, 0, c->plane_words() * 4, c->stream));
+    MPN_TRY(cudaMemsetAsync(c->state.p, 0, c->plane_words() * 16, c->stream));
     MPN_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Ctl), c->stream));
     return MPN_OK;
 }
@@ -425,8 +421,6 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     mpn_status st = begin_propagate(c, targets, n, &dt);
     if (st != MPN_OK) return st;
     const size_t ntiles = (size_t)c->ntx * c->nty;
-    MPN_TRY(cudaMemsetAsync(c->nb0.p, 0, c->plane_words() * 4, c->stream));
-    MPN_TRY(cudaMemsetAsync(c->nb1.p, 0, c->plane_words() * 4, c->stream));
     MPN_TRY(cudaMemsetAsync(c->tiles.p, 0, ntiles * sizeof(uint32_t), c->stream));
     PropParams p{};
     p.g = c->grid();
@@ -732,7 +726,7 @@ mpn_status mpn_get_stats(mpn_ctx *c, mpn_stats *out) {
 void mpn_destroy(mpn_ctx *c) {
     if (!c) return;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) cudaGetLastError();
-    DevBuf *bufs[] = {&c->free_bits, &c->vis, &c->nb0, &c->nb1, &c->dist, &c->ctl, &c->tiles,
+    DevBuf *bufs[] = {&c->free_bits, &c->state, &c->dist, &c->ctl, &c->tiles,
                       &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
                       &c->cells, &c->activity};
     for (DevBuf *b : bufs) b->release();

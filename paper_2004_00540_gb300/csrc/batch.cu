@@ -125,7 +125,8 @@ __global__ void k_batch_seed(BatchParams p, const SeedJob *jobs) {
         }
         if (d.dist_bits == 16) reinterpret_cast<uint16_t *>(d.g.dist)[t] = 0;
         else reinterpret_cast<uint32_t *>(d.g.dist)[t] = 0u;
-        atomicOr(d.g.vis + wo, bit);
+        atomicOr(d.g.state + 4 * wo, bit);   // V of both pairs
+        atomicOr(d.g.state + 4 * wo + 2, bit);
         const int ty = y / d.TY, tx = (x >> 5) / d.TXW;
         const int ri = y - ty * d.TY, wi = (x >> 5) - tx * d.TXW;
         push_zone_b(p, d, job.slot, ty, tx, wave::border_bits(ri, wi, bit, d.k, d.TY, d.TXW), S);
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             const uint32_t maxl = dref.max_layers;
             v.jmax = v.k;
             if (maxl && v.l0 + (uint32_t)v.k > maxl) v.jmax = (int)(maxl - v.l0);
-            v.nbS = (s & 1) ? v.g.nb1 : v.g.nb0;
+            v.par = (int)(s & 1u);
             uint32_t fmask = 0u;
             unsigned lastj = 0u;
             if (valid) wave::visit_tile<RXW, R, NW>(v, sm, &p.descs[slot].err, &fmask, &lastj);
@@ -537,7 +538,7 @@ mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_
     m.nt = nt;
     m.ns = ns;
     const size_t plane = align_up((size_t)H * m.P * 4);
-    m.planes_bytes = 4 * plane;
+    m.planes_bytes = 5 * plane;   // free bits + propagation state (4 words per word)
     m.dist_o = 0;
     m.tgt_o = align_up((size_t)H * W * (dist_bits / 8));
     m.st_o = m.tgt_o + align_up((size_t)nt * 4);
@@ -580,10 +581,10 @@ mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_
         e = cudaMemcpyAsync((void *)dmask, mask, (size_t)H * W, cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess) e = launch_pack(dmask, H, W, m.P, fb, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync((char *)fb + plane, 0, 3 * plane, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync((char *)fb + plane, 0, 4 * plane, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(res + m.dist_o, 0xff, (size_t)H * W * (dist_bits / 8), st);
     // reject bad end-points now, so that no grid can fail while in flight
-    uint32_t *flag = (uint32_t *)((char *)fb + plane);   // one word of the zeroed visit plane
+    uint32_t *flag = (uint32_t *)((char *)fb + plane);   // one word of the zeroed state
     if (e == cudaSuccess) {
         const int n = nt > ns ? nt : ns;
         count_launch();
@@ -678,7 +679,7 @@ static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t 
     char *res = (char *)arena_at(b, m.res_off);
     GridDev g;
     g.free_bits = nullptr;
-    g.vis = g.nb0 = g.nb1 = nullptr;
+    g.state = nullptr;
     g.dist = res + m.dist_o;
     g.H = m.H;
     g.W = m.W;
@@ -723,7 +724,7 @@ static mpn_status finish_round(mpn_batch *b) {
             char *res = (char *)arena_at(b, m->res_off);
             GridDev g;
             g.free_bits = (const uint32_t *)arena_at(b, m->planes_off);
-            g.vis = g.nb0 = g.nb1 = nullptr;
+            g.state = nullptr;
             g.dist = res + m->dist_o;
             g.H = m->H;
             g.W = m->W;
@@ -777,11 +778,9 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, 
         if (m.state != MState::Admitted) continue;
         MazeDesc d{};
         char *res = (char *)arena_at(b, m.res_off);
-        const size_t plane = m.planes_bytes / 4;
+        const size_t plane = m.planes_bytes / 5;
         d.g.free_bits = (const uint32_t *)arena_at(b, m.planes_off);
-        d.g.vis = (uint32_t *)((char *)arena_at(b, m.planes_off) + plane);
-        d.g.nb0 = (uint32_t *)((char *)arena_at(b, m.planes_off) + 2 * plane);
-        d.g.nb1 = (uint32_t *)((char *)arena_at(b, m.planes_off) + 3 * plane);
+        d.g.state = (uint32_t *)((char *)arena_at(b, m.planes_off) + plane);
         d.g.dist = res + m.dist_o;
         d.g.H = m.H;
         d.g.W = m.W;

@@ -38,10 +38,16 @@ struct Ctl {
 
 // Bit planes and distance plane of one grid. Bit b of word w in row y is cell
 // x = 32 * w + b; rows are P words apart (P a multiple of 4).
+//
+// The propagation state keeps four words per plane word o, at state[4 * o]:
+// {V, N0, V, N1}. V = reached; Np = the cells that the last sweep of parity p
+// to change the word reached in it (0 after a sweep of the other parity
+// changed it). Each {V, Np} pair is stored and loaded as one 64-bit access, so
+// a reader always gets a word's reached bits together with the matching
+// this-sweep bits, and neither side needs a fence.
 struct GridDev {
     const uint32_t *free_bits;   // 1 = free; bits at x >= W are 0
-    uint32_t *vis;               // 1 = reached
-    uint32_t *nb0, *nb1;         // cells first reached in the last sweep of that parity
+    uint32_t *state;             // 4 * H * P words, see above
     void *dist;                  // H*W uint16 or uint32, row-major, pitch W
     int H, W, P;
 };

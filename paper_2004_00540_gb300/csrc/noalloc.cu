@@ -8,7 +8,7 @@
 // lives in one file-scope device array of fixed size instead.
 //
 // That array belongs to every GPU that loads this library, from load until the
-// process exits (about 2.1 MB). Calls share it and it keeps the last call's
+// process exits (about 2.6 MB). Calls share it and it keeps the last call's
 // contents, so each call clears what must start at zero, and two calls whose
 // GPU work overlaps (different streams, or different host threads) race on it.
 #include <cstring>
@@ -33,10 +33,10 @@ constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kNaPlaneBytes = align256(kNaPlaneWords * sizeof(uint32_t));
 constexpr size_t kNaTileBytes = align256(kNaMaxTiles * 4 * sizeof(uint32_t));
 constexpr size_t kNaCtlBytes = align256(sizeof(Ctl));
-constexpr size_t kNaScratchBytes = 4 * kNaPlaneBytes + kNaTileBytes + kNaCtlBytes;
+constexpr size_t kNaScratchBytes = 5 * kNaPlaneBytes + kNaTileBytes + kNaCtlBytes;
 
-// The scratch: free bits, visit bits, two this-sweep bit planes, the tile
-// queue, the control block. In host code this name is only a stand-in for the
+// The scratch: free bits, the propagation state (four words per plane word),
+// the tile queue, the control block. In host code this name is only a stand-in for the
 // device array; the kernels get the address cudaGetSymbolAddress returns.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
 
@@ -91,17 +91,13 @@ extern "C" mpn_status mpn_propagate_noalloc(const uint8_t *mask, int32_t H, int3
     if (e != cudaSuccess || bps < 1) return MPN_ECUDA;
 
     uint32_t *free_bits = reinterpret_cast<uint32_t *>(base);
-    uint32_t *vis = reinterpret_cast<uint32_t *>(base + kNaPlaneBytes);
-    uint32_t *nb0 = reinterpret_cast<uint32_t *>(base + 2 * kNaPlaneBytes);
-    uint32_t *nb1 = reinterpret_cast<uint32_t *>(base + 3 * kNaPlaneBytes);
-    uint32_t *tiles = reinterpret_cast<uint32_t *>(base + 4 * kNaPlaneBytes);
-    Ctl *ctl = reinterpret_cast<Ctl *>(base + 4 * kNaPlaneBytes + kNaTileBytes);
+    uint32_t *state = reinterpret_cast<uint32_t *>(base + kNaPlaneBytes);
+    uint32_t *tiles = reinterpret_cast<uint32_t *>(base + 5 * kNaPlaneBytes);
+    Ctl *ctl = reinterpret_cast<Ctl *>(base + 5 * kNaPlaneBytes + kNaTileBytes);
     const size_t plane_bytes = (size_t)H * P * sizeof(uint32_t);
 
     // what must start at zero (the array keeps the previous call's contents)
-    e = cudaMemsetAsync(vis, 0, plane_bytes, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(nb0, 0, plane_bytes, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(nb1, 0, plane_bytes, st);
+    e = cudaMemsetAsync(state, 0, 4 * plane_bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(tiles, 0, ntiles * sizeof(uint32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dist, 0xff, (size_t)H * W * sizeof(uint32_t), st);
@@ -110,9 +106,7 @@ extern "C" mpn_status mpn_propagate_noalloc(const uint8_t *mask, int32_t H, int3
 
     PropParams p{};
     p.g.free_bits = free_bits;
-    p.g.vis = vis;
-    p.g.nb0 = nb0;
-    p.g.nb1 = nb1;
+    p.g.state = state;
     p.g.dist = dist;
     p.g.H = H;
     p.g.W = W;

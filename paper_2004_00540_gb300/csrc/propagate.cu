@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
         v.l0 = l0;
         v.jmax = p.k;
         if (p.max_layers && l0 + (uint32_t)p.k > p.max_layers) v.jmax = (int)(p.max_layers - l0);
-        v.nbS = (s & 1) ? p.g.nb1 : p.g.nb0;
+        v.par = (int)(s & 1u);
         const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
         unsigned *work = &ctl->work[s % 3];
         const uint32_t len = s_len;
@@ -256,22 +256,20 @@ __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int 
 }
 
 // Block = NW consumer warps + 1 producer warp. The producer (lane 0 of the
-// last warp) claims tiles, loads each claimed tile's region -- free bits and
-// visit bits, then, once the visit bits have landed, this-sweep bits -- with
-// TMA into one of two shared-memory buffers, and queues the tiles a finished
-// visit reaches. The consumer warps take each buffer in turn, run the tile's
-// layers in registers (named barrier 1 only) and write back. So the next
-// tile's region arrives while the current one is computed, and claims and
-// queue pushes never stall the consumer warps. A TMA box starts at a word
-// coordinate rounded down to a multiple of 4 (16-byte rule) and is 12 words
-// wide; the region's 8 words start xoff = 0..3 words into it. Boxes outside
-// the grid (negative or past the edge) are filled with zeros.
+// last warp) claims tiles, loads each claimed tile's free bits with TMA into
+// one of two shared-memory buffers, and queues the tiles a finished visit
+// reaches. The consumer warps take each buffer in turn, load the region's
+// propagation state themselves ({V, Npar} pairs, which must be read as 64-bit
+// accesses), run the tile's layers in registers (named barrier 1 only) and
+// write back. So the next tile's free bits arrive while the current one is
+// computed, and claims and queue pushes never stall the consumer warps. A TMA
+// box starts at a word coordinate rounded down to a multiple of 4 (16-byte
+// rule) and is 12 words wide; the region's 8 words start xoff = 0..3 words
+// into it. Boxes outside the grid (negative or past the edge) are filled with
+// zeros.
 template <int RXW, int R, int NW>
 __global__ void __launch_bounds__((NW + 1) * 32, 2)
-    k_propagate_tma(const __grid_constant__ CUtensorMap tm_free,
-                    const __grid_constant__ CUtensorMap tm_vis,
-                    const __grid_constant__ CUtensorMap tm_nb0,
-                    const __grid_constant__ CUtensorMap tm_nb1, PropParams p) {
+    k_propagate_tma(const __grid_constant__ CUtensorMap tm_free, PropParams p) {
     constexpr int GPW = 32 / RXW;
     constexpr int RY = NW * GPW * R;
     constexpr int BW = ((RXW + 3) + 3) / 4 * 4;   // box width in words
@@ -280,9 +278,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
     static_assert(RY <= 256, "TMA box height");
 
     __shared__ __align__(128) uint32_t sF[2][RY * BW];
-    __shared__ __align__(128) uint32_t sV[2][RY * BW];
-    __shared__ __align__(128) uint32_t sN[2][RY * BW];
-    __shared__ __align__(8) uint64_t full[2], vfull[2], done[2];
+    __shared__ __align__(8) uint64_t full[2], done[2];
     __shared__ int s_tile[2], s_xoff[2], s_ctile;
     __shared__ unsigned s_fmask[2], s_done, s_maxl, s_ok;
     __shared__ uint32_t s_len;
@@ -296,13 +292,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
     unsigned thr_maxl = 0u;
     unsigned long long visits = 0;   // producer lane 0
     uint32_t q = 0;                  // slot uses so far (same sequence on both sides)
-    uint32_t pf = 0, pv = 0, pd = 0; // phase bits per buffer (bit b)
+    uint32_t pf = 0, pd = 0;         // phase bits per buffer (bit b)
 
     sm.zero_pad();
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&full[b], 1);
-            mbar_init(&vfull[b], 1);
             mbar_init(&done[b], 1);
             s_fmask[b] = 0u;
         }
@@ -332,8 +327,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
         v.l0 = l0;
         v.jmax = p.k;
         if (p.max_layers && l0 + (uint32_t)p.k > p.max_layers) v.jmax = (int)(p.max_layers - l0);
-        v.nbS = (s & 1) ? p.g.nb1 : p.g.nb0;
-        const CUtensorMap *tm_nb = (s & 1) ? &tm_nb1 : &tm_nb0;
+        v.par = (int)(s & 1u);
         const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
         unsigned *work = &ctl->work[s % 3];
         const uint32_t len = s_len;
@@ -351,17 +345,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
                     const int ty = t / p.ntx, tx = t - ty * p.ntx;
                     const int gw0 = tx * p.TXW - 1, x0 = gw0 & ~3, y0 = ty * p.TY - p.k;
                     s_xoff[b] = gw0 - x0;
-                    mbar_arrive_tx(&vfull[b], BOX_BYTES);
-                    tma_load(sV[b], &tm_vis, x0, y0, &vfull[b]);
-                    mbar_arrive_tx(&full[b], 2 * BOX_BYTES);
+                    mbar_arrive_tx(&full[b], BOX_BYTES);
                     tma_load(sF[b], &tm_free, x0, y0, &full[b]);
-                    // this-sweep bits only after the visit bits: a bit new in
-                    // this sweep is then always masked
-                    const bool ok = mbar_wait(&vfull[b], (pv >> b) & 1u);
-                    pv ^= 1u << b;
-                    __threadfence();
-                    tma_load(sN[b], tm_nb, x0, y0, &full[b]);
-                    return ok;
+                    return true;
                 };
                 auto claim = [&]() -> int {
                     const uint32_t i = G + atomicAdd(work, 1u);
@@ -395,25 +381,18 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
                 const int b = (int)(q & 1u);
                 if (threadIdx.x == 0) {
                     int t = -1;
-                    if (mbar_wait(&full[b], (pf >> b) & 1u)) {
-                        t = s_tile[b];
-                        if (t >= 0 && !mbar_wait(&vfull[b], (pv >> b) & 1u)) t = -1;
-                    }
+                    if (mbar_wait(&full[b], (pf >> b) & 1u)) t = s_tile[b];
+                    else atomicOr(&ctl->err, ERR_TIMEOUT);
                     s_ctile = t;
                 }
                 wave::bar_sync<true, NBAR>();
                 const int t = s_ctile;
-                if (t >= 0) {
-                    // every consumer acquires the staged buffer itself (both
-                    // phases are complete: thread 0 saw them, so these return
-                    // at once)
-                    mbar_wait(&full[b], (pf >> b) & 1u);
-                    mbar_wait(&vfull[b], (pv >> b) & 1u);
-                }
+                // every consumer acquires the staged buffer itself (the phase
+                // is complete: thread 0 saw it, so this returns at once)
+                if (t >= 0) mbar_wait(&full[b], (pf >> b) & 1u);
                 pf ^= 1u << b;
                 ++q;
                 if (t < 0) break;
-                pv ^= 1u << b;
                 // ---- the region from the staged buffer ----
                 const int w = lane % RXW;
                 const int g = wave::row_group<RXW, NW>(warp, lane);
@@ -422,26 +401,27 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
                 v.tx = t - v.ty * p.ntx;
                 const int xo = s_xoff[b] + w;
                 const bool ownW = (w >= 1) && (w <= p.TXW);
+                const int gw = v.tx * p.TXW - 1 + w;
+                const int y0 = v.ty * p.TY - p.k;
                 uint32_t V[R], F[R], OWN[R];
 #pragma unroll
                 for (int i = 0; i < R; ++i) {
-                    const int rr = r0 + i;
+                    const int rr = r0 + i, y = y0 + rr;
                     const bool own = ownW && rr >= p.k && rr < p.k + p.TY;
+                    const bool in = gw >= 0 && gw < p.g.P && y >= 0 && y < p.g.H;
                     OWN[i] = own ? 0xffffffffu : 0u;
                     F[i] = sF[b][rr * BW + xo];
-                    const uint32_t vv = sV[b][rr * BW + xo];
-                    V[i] = own ? vv : (vv & ~sN[b][rr * BW + xo]);
+                    const uint64_t vn =
+                        in ? wave::ld_pair(p.g.state + 4 * ((size_t)y * p.g.P + gw) + 2 * v.par) : 0ull;
+                    V[i] = (uint32_t)vn & (own ? 0xffffffffu : ~(uint32_t)(vn >> 32));
                 }
                 uint32_t fmask;
                 unsigned lastj;
                 wave::visit_core<RXW, R, NW, true>(v, sm, &ctl->err, V, F, OWN, &fmask, &lastj);
                 if (fmask) atomicOr(&s_fmask[b], fmask);
                 if (lastj) thr_maxl = max(thr_maxl, l0 + lastj);
-                wave::bar_sync<true, NBAR>();   // all zones in, all global writes issued
-                if (threadIdx.x == 0) {
-                    asm volatile("fence.proxy.async.global;" ::: "memory");
-                    mbar_arrive(&done[b]);
-                }
+                wave::bar_sync<true, NBAR>();   // all zones in
+                if (threadIdx.x == 0) mbar_arrive(&done[b]);   // (TMA reads only the read-only free bits)
             }
         }
 
@@ -491,7 +471,8 @@ __global__ void k_seed(const uint32_t *targets, int n, PropParams p) {
         return;
     }
     reinterpret_cast<DT *>(g.dist)[t] = (DT)0;
-    atomicOr(g.vis + wo, bit);
+    atomicOr(g.state + 4 * wo, bit);       // V of both pairs
+    atomicOr(g.state + 4 * wo + 2, bit);
     if (p.lists) {
         const int ty = y / p.TY, tx = (x >> 5) / p.TXW;
         const int ri = y - ty * p.TY, wi = (x >> 5) - tx * p.TXW;
@@ -636,13 +617,10 @@ cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int bloc
     }
     const VariantDesc &d = kVariants[v];
     const int ry = d.nwarps * (32 / d.rxw) * d.r, bw = (d.rxw + 6) / 4 * 4;
-    CUtensorMap mf, mv, m0, m1;
+    CUtensorMap mf;
     cudaError_t e = plane_map(&mf, p.g.free_bits, p.g.P, p.g.H, bw, ry);
-    if (e == cudaSuccess) e = plane_map(&mv, p.g.vis, p.g.P, p.g.H, bw, ry);
-    if (e == cudaSuccess) e = plane_map(&m0, p.g.nb0, p.g.P, p.g.H, bw, ry);
-    if (e == cudaSuccess) e = plane_map(&m1, p.g.nb1, p.g.P, p.g.H, bw, ry);
     if (e != cudaSuccess) return e;
-    void *args[] = {&mf, &mv, &m0, &m1, &pp};
+    void *args[] = {&mf, &pp};
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(variant_threads(v)), args, 0, st);
 }
 

@@ -33,6 +33,19 @@ __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// A {V, Np} pair of the propagation state as one 64-bit access (V in the low
+// word).
+__device__ __forceinline__ uint64_t ld_pair(const uint32_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_pair(uint32_t *p, uint32_t v, uint32_t n) {
+    const uint64_t x = (uint64_t)v | ((uint64_t)n << 32);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
+}
+
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -138,7 +151,7 @@ __device__ __forceinline__ void bar_sync() {
 // One tile visit's inputs.
 struct Visit {
     GridDev g;            // planes of the grid the tile belongs to
-    uint32_t *nbS;        // this-sweep plane of the sweep's parity
+    int par;              // parity of the sweep: the visit reads {V, Npar}
     int dist_bits;        // 16 or 32
     int TY, TXW, k;       // tile geometry and depth
     int ty, tx;           // tile coordinates within its grid
@@ -227,48 +240,59 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     // inner rows overlap the wait at the barrier), the group's top and bottom
     // rows exchanged through shared memory, then a row's new bits are the
     // vertical OR of three dilated rows within the free cells. The bits a
-    // visit reaches are recovered at the end against V0. Layers run in pairs:
-    // an even layer records whether it changed anything and the next odd
-    // layer's barrier ORs that over the block and ends the visit if nothing
-    // did (a stable region costs at most one extra layer); the row groups at
-    // the region's top and bottom edge read a zero exchange slot.
+    // visit reaches are recovered at the end against V0. Layers run in
+    // fours (j = 1, 2, 3, 0 mod 4), so the Gray plane of three of them is
+    // known at compile time; a layer j = 0 mod 4 records whether it changed
+    // anything and the next layer's barrier ORs that over the block and ends
+    // the visit if nothing did (a stable region costs at most three extra
+    // layers). The row groups at the region's top and bottom edge read a
+    // zero exchange slot.
     uint32_t changed = 1u;
     unsigned lastj = 0u;
-    // one layer with the exchange slots of its parity; false: region stable
-    auto layer = [&](uint32_t *xt, uint32_t *xb, auto odd) -> bool {
+    // one layer with the exchange slots of its parity; false: region stable.
+    // kind (compile time): check the stability flag, record it, or neither.
+    using Check = std::integral_constant<int, 1>;
+    using Record = std::integral_constant<int, 0>;
+    using Plain = std::integral_constant<int, 2>;
+    auto layer = [&](uint32_t *xt, uint32_t *xb, auto kind) -> bool {
         uint32_t h[R];
 #pragma unroll
         for (int i = 0; i < R; ++i) h[i] = hdil<RXW>(V[i]);
         xt[slot] = h[0];
         xb[slot] = h[R - 1];
-        if (decltype(odd)::value) {
+        if (decltype(kind)::value == Check::value) {
             if (!bar_or<NAMED, NBAR>(changed != 0u)) return false;
         } else {
             bar_sync<NAMED, NBAR>();
         }
         const uint32_t hUp = xb[slot_up];
         const uint32_t hDn = xt[slot_dn];
-        if (!decltype(odd)::value) changed = 0u;
+        if (decltype(kind)::value == Record::value) changed = 0u;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             const uint32_t up = (i > 0) ? h[i - 1] : hUp;
             const uint32_t dn = (i < R - 1) ? h[i + 1] : hDn;
             const uint32_t vn = V[i] | ((up | h[i] | dn) & F[i]);
-            if (!decltype(odd)::value) changed |= vn ^ V[i];
+            if (decltype(kind)::value == Record::value) changed |= vn ^ V[i];
             V[i] = vn;
         }
         return true;
     };
     // unreached cells: gray(j - 1) -> gray(j), plane ctz(j)
 #define MPN_FLIP(B) _Pragma("unroll") for (int i = 0; i < R; ++i) P[B][i] ^= ~V[i]
-    for (int j = 1; j <= v.jmax; j += 2) {   // j odd: ctz(j) = 0
-        if (!layer(sm.xtop[1], sm.xbot[1], std::true_type())) break;
+    for (int j = 1; j <= v.jmax; j += 4) {   // j = 1 mod 4
+        if (!layer(sm.xtop[1], sm.xbot[1], Check())) break;
         if (j == v.jmax) break;
         MPN_FLIP(0);
-        if (!layer(sm.xtop[0], sm.xbot[0], std::false_type())) break;
+        if (!layer(sm.xtop[0], sm.xbot[0], Plain())) break;
         if (j + 1 == v.jmax) break;
-        switch (__ffs(j + 1) - 1) {   // 1..4 (j + 1 < 32), block-uniform
-            case 1: MPN_FLIP(1); break;
+        MPN_FLIP(1);
+        if (!layer(sm.xtop[1], sm.xbot[1], Plain())) break;
+        if (j + 2 == v.jmax) break;
+        MPN_FLIP(0);
+        if (!layer(sm.xtop[0], sm.xbot[0], Record())) break;
+        if (j + 3 == v.jmax) break;
+        switch (__ffs(j + 3) - 1) {   // 2..4 (j + 3 < 32), block-uniform
             case 2: MPN_FLIP(2); break;
             case 3: MPN_FLIP(3); break;
             default: MPN_FLIP(4); break;
@@ -351,20 +375,24 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
         }
     }
 
-    // ---- publish: this-sweep bits, then visit bits ----
+    // ---- publish: {V, this sweep's new bits} for this parity, {V, 0} for
+    // the other (a later sweep of that parity sees no stale bits of this word)
 #pragma unroll
-    for (int i = 0; i < R; ++i)
-        if (NB[i]) st_relaxed(v.nbS + (size_t)(y0 + r0 + i) * gd.P + gw, NB[i]);
-    __threadfence();
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-        if (NB[i]) st_relaxed(gd.vis + (size_t)(y0 + r0 + i) * gd.P + gw, V[i]);
+    for (int i = 0; i < R; ++i) {
+        if (!NB[i]) continue;
+        uint32_t *st = gd.state + 4 * ((size_t)(y0 + r0 + i) * gd.P + gw);
+        st_pair(st + 2 * v.par, V[i], NB[i]);
+        st_pair(st + 2 * (v.par ^ 1), V[i], 0u);
+    }
 }
 
 // A tile visit that loads its own region from global memory (the
 // register-only kernels). Halo words of other tiles are read as of the start
-// of the sweep: their this-sweep bits are masked out (the owner writes those
-// before its visit bits; the fences order both sides).
+// of the sweep: the {V, Npar} pair comes in one load, and a word that its
+// owner changed in this sweep has exactly the bits new in this sweep in Npar.
+// (A word last changed two or more sweeps back may still carry that sweep's
+// bits in Npar; those cells' whole neighbourhoods were reached by then, so
+// hiding them changes nothing inside the tile.)
 template <int RXW, int R, int NW>
 __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
                                            uint32_t *fmask_out, unsigned *lastj_out) {
@@ -387,12 +415,9 @@ __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &s
         const size_t off = (size_t)y * gd.P + gw;
         OWN[i] = own ? 0xffffffffu : 0u;
         F[i] = in ? __ldg(gd.free_bits + off) : 0u;
-        V[i] = in ? ld_relaxed(gd.vis + off) : 0u;
+        const uint64_t vn = in ? ld_pair(gd.state + 4 * off + 2 * v.par) : 0ull;
+        V[i] = (uint32_t)vn & (own ? 0xffffffffu : ~(uint32_t)(vn >> 32));
     }
-    __threadfence();   // visit bits before the matching this-sweep bits
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-        if (!OWN[i] && V[i]) V[i] &= ~ld_relaxed(v.nbS + (size_t)(y0 + r0 + i) * gd.P + gw);
     visit_core<RXW, R, NW, false>(v, sm, err, V, F, OWN, fmask_out, lastj_out);
 }
 

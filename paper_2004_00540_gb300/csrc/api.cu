@@ -139,7 +139,7 @@ struct mpn_ctx {
     int device = 0, sm_count = 0;
     cudaStream_t stream = nullptr;
 
-    DevBuf free_bits, state, dist, ctl, tiles, mask_stage;
+    DevBuf free_bits, state, dist, ctl, tiles, mask_stage, log, log_fill;
     DevBuf targets, starts, offsets, status, cells, activity;
 
     int variant = 0, depth = 32;
@@ -422,6 +422,20 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     if (st != MPN_OK) return st;
     const size_t ntiles = (size_t)c->ntx * c->nty;
     MPN_TRY(cudaMemsetAsync(c->tiles.p, 0, ntiles * sizeof(uint32_t), c->stream));
+    // activation log: room for 1.5 entries per plane word plus one partly
+    // filled chunk per block (a block that finds it full writes distances
+    // itself, so the size only affects speed)
+    const uint64_t log_entries = c->plane_words() * 3 / 2 + (uint64_t)c->blocks * kLogChunk;
+    uint32_t log_chunks = (uint32_t)((log_entries + kLogChunk - 1) / kLogChunk);
+    if (c->log.ensure((size_t)log_chunks * kLogFields * kLogChunk * sizeof(uint32_t)) != cudaSuccess ||
+        c->log_fill.ensure((size_t)log_chunks * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();   // no room for the log: the kernel writes distances itself
+        c->log.release();
+        c->log_fill.release();
+        log_chunks = 0;
+    }
+    if (log_chunks)
+        MPN_TRY(cudaMemsetAsync(c->log_fill.p, 0, (size_t)log_chunks * sizeof(uint32_t), c->stream));
     PropParams p{};
     p.g = c->grid();
     p.queued = (uint32_t *)c->tiles.p;
@@ -434,11 +448,15 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     p.TXW = c->TXW;
     p.max_layers = max_layers;
     p.spin_limit = kSpinLimit;
+    p.log = log_chunks ? (uint32_t *)c->log.p : nullptr;
+    p.log_fill = (uint32_t *)c->log_fill.p;
+    p.log_chunks = log_chunks;
     const uint64_t bound = (max_layers ? (uint64_t)max_layers : (uint64_t)c->H * c->W) / c->depth + 3;
     p.sweep_cap = (uint32_t)(bound < (1u << 22) ? bound : (1u << 22));
     MPN_TRY(launch_seed(dt, n, p, c->dist_bits, c->stream));
-    MPN_TRY(cudaEventRecord(c->ev[2], c->stream));   // times the persistent kernel alone
+    MPN_TRY(cudaEventRecord(c->ev[2], c->stream));   // times the persistent kernel + log decode
     MPN_TRY(launch_propagate(c->variant, c->dist_bits, p, c->blocks, c->stream));
+    MPN_TRY(launch_log_decode(p, c->dist_bits, c->stream));
     MPN_TRY(cudaEventRecord(c->ev[3], c->stream));
     c->ev_prop = true;
     c->stats_pending = true;
@@ -726,7 +744,7 @@ mpn_status mpn_get_stats(mpn_ctx *c, mpn_stats *out) {
 void mpn_destroy(mpn_ctx *c) {
     if (!c) return;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) cudaGetLastError();
-    DevBuf *bufs[] = {&c->free_bits, &c->state, &c->dist, &c->ctl, &c->tiles,
+    DevBuf *bufs[] = {&c->free_bits, &c->state, &c->log, &c->log_fill, &c->dist, &c->ctl, &c->tiles,
                       &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
                       &c->cells, &c->activity};
     for (DevBuf *b : bufs) b->release();

@@ -26,7 +26,7 @@ constexpr uint32_t FB_NW = 32u, FB_NE = 64u, FB_SW = 128u, FB_SE = 256u;
 // Device control block of one propagation (zeroed before each run).
 struct Ctl {
     unsigned int bar_count;        // grid-barrier arrivals of this launch (monotonic)
-    unsigned int bar_gen;          // unused
+    unsigned int log_next;         // next free chunk of the activation log
     unsigned int work[3];          // claim counters of the tile lists, by sweep mod 3
     unsigned int list_len[3];      // lengths of the tile lists, by sweep mod 3
     unsigned int err;
@@ -64,7 +64,22 @@ struct PropParams {
     uint32_t max_layers;         // 0 = until nothing changes
     uint32_t spin_limit;         // barrier wait limit (iterations of ~100 ns)
     uint32_t sweep_cap;          // more sweeps than this is an error
+    uint32_t *log;               // activation log (log_chunks chunks), or null
+    uint32_t *log_fill;          // entries written per chunk
+    uint32_t log_chunks;
 };
+
+// Activation log: instead of writing distances during a tile visit, the visit
+// records, for every word of its interior in which it reached cells, one
+// entry of kLogFields words -- the word's first cell index (y * W + 32 * word
+// column), the layer of offset 0 (l0 + 1), the reached bits and the five
+// Gray-code counter planes -- and k_log_decode turns the entries into
+// distances after the propagation. A chunk holds kLogChunk entries as
+// kLogFields arrays of kLogChunk words (so a warp's entries are written with
+// coalesced stores); each block fills chunks it takes from a shared pool, and
+// a block that finds the pool empty writes its distances directly.
+constexpr uint32_t kLogChunk = 4096;
+constexpr uint32_t kLogFields = 8;
 
 struct VariantDesc {
     int rxw;      // region words (lanes per row group)
@@ -91,6 +106,7 @@ int variant_threads(int v);   // threads per block of variant v
 cudaError_t propagate_blocks_per_sm(int v, int dist_bits, int *out);
 cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int blocks,
                              cudaStream_t st);
+cudaError_t launch_log_decode(const PropParams &p, int dist_bits, cudaStream_t st);
 cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int dist_bits,
                         cudaStream_t st);
 cudaError_t launch_plain_layer(const GridDev &g, int dist_bits, uint32_t layer, Ctl *ctl,

@@ -80,12 +80,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     __shared__ int s_tile;
     __shared__ unsigned s_mask[2], s_done, s_maxl, s_ok;   // s_mask by visit parity
     __shared__ uint32_t s_len;                              // length of this sweep's list
+    __shared__ int s_chunk;                                 // activation-log chunk, -1: none
+    __shared__ unsigned s_cursor;                           // entries used in it
 
     const int ntiles = p.ntx * p.nty;
     Ctl *ctl = p.ctl;
     unsigned thr_maxl = 0u;              // largest layer this thread's words reached
     unsigned long long blk_visits = 0;   // thread 0: tile visits of this block
     unsigned vq = 0u;                    // visit parity (block-uniform)
+    bool log_more = p.log != nullptr;    // thread 0: the pool may still have chunks
+    const uint32_t maxv = (uint32_t)(p.TY * p.TXW);   // log entries one visit can need
+    const wave::LogSink lg{p.log, &s_chunk, &s_cursor};
 
     sm.zero_pad();   // (the first barrier below publishes it)
     // the seeding step rejected the targets (nothing in this kernel sets these
@@ -104,6 +109,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
         // sweep 0: entry blockIdx.x of the seeded list is this block's first tile
         s_len = ld_acquire(&ctl->list_len[0]);
         s_tile = (blockIdx.x < s_len) ? (int)ld_relaxed(p.lists + blockIdx.x) : -1;
+        s_chunk = -1;
+        s_cursor = 0u;
     }
     __syncthreads();
     for (uint32_t s = 0;; ++s) {
@@ -140,12 +147,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             if (threadIdx.x == 0) {
                 next_i = G + atomicAdd(work, 1u);
                 s_mask[vq] = 0u;   // last read two visits ago, before the previous visit's first barrier
+                if (log_more && (s_chunk < 0 || s_cursor + maxv > kLogChunk)) {
+                    // this chunk may not hold the visit's entries: take the next one
+                    if (s_chunk >= 0) p.log_fill[s_chunk] = s_cursor;
+                    const uint32_t c = atomicAdd(&ctl->log_next, 1u);
+                    log_more = c < p.log_chunks;
+                    s_chunk = log_more ? (int)c : -1;
+                    s_cursor = 0u;
+                }
             }
             v.ty = t / p.ntx;
             v.tx = t - v.ty * p.ntx;
             uint32_t fmask;
             unsigned lastj;
-            wave::visit_tile<RXW, R, NW>(v, sm, &ctl->err, &fmask, &lastj);
+            wave::visit_tile<RXW, R, NW>(v, sm, &ctl->err, &fmask, &lastj, lg);
             uint32_t pend_i = 0u;
             const bool pend_new = pend_t >= 0 && pend_old < stamp;   // previous visit's push
             if (pend_new) pend_i = atomicAdd(&ctl->list_len[slot1], 1u);
@@ -195,7 +210,62 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             if (thr_maxl) atomicMax(&s_maxl, thr_maxl);
             __syncthreads();
             if (threadIdx.x == 0 && s_maxl) atomicMax(&ctl->max_layer, s_maxl);
+            if (threadIdx.x == 0 && s_chunk >= 0) p.log_fill[s_chunk] = s_cursor;
             return;
+        }
+    }
+}
+
+// Distances from the activation log, after the propagation: a warp takes 32
+// entries (one per lane, coalesced field loads), each lane decodes its entry's
+// 32 cells into shared memory (Gray code -> layer offset), then the warp
+// writes the entries' reached cells one entry at a time, 32 consecutive cells
+// per coalesced store. Entries of one word from different visits hold disjoint
+// reached bits, so the order does not matter. An entry whose first cell lies
+// outside the grid is skipped (defensive; the kernel never writes one).
+template <typename DT>
+__global__ void __launch_bounds__(256) k_log_decode(const uint32_t *log, const uint32_t *fill,
+                                                    const Ctl *ctl, uint32_t chunks, void *dist,
+                                                    uint32_t ncells, uint32_t *err) {
+    __shared__ uint32_t sv[8][32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t used = min(ctl->log_next, chunks);
+    for (uint32_t c = blockIdx.x; c < used; c += gridDim.x) {
+        const uint32_t n = min(fill[c], kLogChunk);
+        const uint32_t *base = log + (size_t)c * (kLogFields * kLogChunk);
+        for (uint32_t g = (uint32_t)warp * 32u; g < n; g += 256u) {
+            const uint32_t e = g + (uint32_t)lane;
+            uint32_t cell0 = 0xffffffffu, nb = 0u, lay = 0u, pl[5] = {0u, 0u, 0u, 0u, 0u};
+            if (e < n) {
+                cell0 = base[e];
+                lay = base[kLogChunk + e];
+                nb = base[2 * kLogChunk + e];
+#pragma unroll
+                for (int b = 0; b < 5; ++b) pl[b] = base[(3 + b) * kLogChunk + e];
+            }
+            if (cell0 >= ncells) nb = 0u;
+#pragma unroll 4
+            for (int x = 0; x < 32; ++x) {
+                uint32_t off = 0u;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) off |= ((pl[b] >> x) & 1u) << b;
+                off ^= off >> 1;
+                off ^= off >> 2;
+                off ^= off >> 4;
+                sv[warp][lane][x] = lay + off;
+            }
+            __syncwarp();
+            const uint32_t m = min(32u, n - g);
+            for (uint32_t j = 0; j < m; ++j) {
+                const uint32_t c0 = __shfl_sync(0xffffffffu, cell0, (int)j);
+                const uint32_t bj = __shfl_sync(0xffffffffu, nb, (int)j);
+                if ((bj >> lane) & 1u) {
+                    const uint32_t layer = sv[warp][j][lane];
+                    if (sizeof(DT) == 2 && layer > 0xfffeu) atomicOr(err, ERR_OVERFLOW);
+                    else reinterpret_cast<DT *>(dist)[c0 + (uint32_t)lane] = (DT)layer;
+                }
+            }
+            __syncwarp();
         }
     }
 }
@@ -622,6 +692,20 @@ cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int bloc
     if (e != cudaSuccess) return e;
     void *args[] = {&mf, &pp};
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(variant_threads(v)), args, 0, st);
+}
+
+cudaError_t launch_log_decode(const PropParams &p, int dist_bits, cudaStream_t st) {
+    if (!p.log || !p.log_chunks) return cudaSuccess;
+    const uint32_t ncells = (uint32_t)((uint64_t)p.g.H * (uint64_t)p.g.W);
+    const int blocks = (int)(p.log_chunks < 152u * 8u ? p.log_chunks : 152u * 8u);
+    count_launch();
+    if (dist_bits == 16)
+        k_log_decode<uint16_t><<<blocks, 256, 0, st>>>(p.log, p.log_fill, p.ctl, p.log_chunks,
+                                                        p.g.dist, ncells, &p.ctl->err);
+    else
+        k_log_decode<uint32_t><<<blocks, 256, 0, st>>>(p.log, p.log_fill, p.ctl, p.log_chunks,
+                                                        p.g.dist, ncells, &p.ctl->err);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int dist_bits,

@@ -177,6 +177,16 @@ __device__ __forceinline__ int xslot(int g, int w) {
     return (g % NW) * 32 + (g / NW) * RXW + w;
 }
 
+// Where a visit leaves its activation records: chunk *s_chunk of the
+// activation log, with *s_cursor entries already used (both in shared memory,
+// set by the block before the visit's first barrier). No log, or
+// *s_chunk < 0: the visit writes its distances itself.
+struct LogSink {
+    uint32_t *log = nullptr;
+    const int *s_chunk = nullptr;
+    unsigned *s_cursor = nullptr;
+};
+
 template <int RXW, int NW>
 struct VisitSmem {
     static constexpr int G = NW * (32 / RXW);
@@ -204,7 +214,7 @@ template <int RXW, int R, int NW, bool NAMED>
 __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
                                            uint32_t (&V)[R], const uint32_t (&F)[R],
                                            const uint32_t (&OWN)[R], uint32_t *fmask_out,
-                                           unsigned *lastj_out) {
+                                           unsigned *lastj_out, const LogSink &lg = LogSink()) {
     constexpr int GPW = 32 / RXW;
     constexpr int G = NW * GPW;
     constexpr int NBAR = NW * 32;
@@ -343,6 +353,35 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     *lastj_out = lastj;
 
     // ---- distances of the cells first reached in this visit ----
+    const int chunk = lg.log ? *lg.s_chunk : -1;   // block-uniform
+    if (chunk >= 0) {
+        // one activation-log entry per changed word: the warp reserves its
+        // entries with one shared-memory atomic and writes them field by field
+        uint32_t *base = lg.log + (size_t)chunk * (kLogFields * kLogChunk);
+        unsigned act[R];
+        uint32_t tot = 0u;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            act[i] = __ballot_sync(0xffffffffu, NB[i] != 0u);
+            tot += (uint32_t)__popc(act[i]);
+        }
+        uint32_t slot = 0u;
+        if (lane == 0 && tot) slot = atomicAdd(lg.s_cursor, tot);
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (NB[i]) {
+                uint32_t *e = base + slot + (uint32_t)__popc(act[i] & below);
+                e[0 * kLogChunk] = (uint32_t)(y0 + r0 + i) * (uint32_t)gd.W + (uint32_t)gw * 32u;
+                e[1 * kLogChunk] = v.l0 + 1u;
+                e[2 * kLogChunk] = NB[i];
+#pragma unroll
+                for (int b = 0; b < 5; ++b) e[(3 + b) * kLogChunk] = P[b][i];
+            }
+            slot += (uint32_t)__popc(act[i]);
+        }
+    } else {
     // The warp writes one changed word at a time: 32 lanes, 32 consecutive
     // cells, one coalesced store.
 #pragma unroll
@@ -375,6 +414,8 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
         }
     }
 
+    }   // log or direct
+
     // ---- publish: {V, this sweep's new bits} for this parity, {V, 0} for
     // the other (a later sweep of that parity sees no stale bits of this word)
 #pragma unroll
@@ -395,7 +436,8 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
 // hiding them changes nothing inside the tile.)
 template <int RXW, int R, int NW>
 __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
-                                           uint32_t *fmask_out, unsigned *lastj_out) {
+                                           uint32_t *fmask_out, unsigned *lastj_out,
+                                           const LogSink &lg = LogSink()) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = lane % RXW;
     const int g = row_group<RXW, NW>(warp, lane);
@@ -418,7 +460,7 @@ __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &s
         const uint64_t vn = in ? ld_pair(gd.state + 4 * off + 2 * v.par) : 0ull;
         V[i] = (uint32_t)vn & (own ? 0xffffffffu : ~(uint32_t)(vn >> 32));
     }
-    visit_core<RXW, R, NW, false>(v, sm, err, V, F, OWN, fmask_out, lastj_out);
+    visit_core<RXW, R, NW, false>(v, sm, err, V, F, OWN, fmask_out, lastj_out, lg);
 }
 
 }  // namespace wave

@@ -216,18 +216,26 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     }
 }
 
-// Distances from the activation log, after the propagation: a warp takes 32
-// entries (one per lane, coalesced field loads), each lane decodes its entry's
-// 32 cells into shared memory (Gray code -> layer offset), then the warp
-// writes the entries' reached cells one entry at a time, 32 consecutive cells
-// per coalesced store. Entries of one word from different visits hold disjoint
-// reached bits, so the order does not matter. An entry whose first cell lies
-// outside the grid is skipped (defensive; the kernel never writes one).
+// Distances from the activation log, after the propagation: a block takes a
+// chunk, a warp 32 entries of it at a time (one per lane, coalesced field
+// loads); each lane turns its entry's
+// Gray planes into binary planes (four XORs for all 32 cells) and packs the
+// 32 layer offsets as bytes into shared memory (four cells per word: each
+// plane's nibble is spread to one bit per byte with a multiply), then the
+// warp writes the entries' reached cells one entry at a time, 32 consecutive
+// cells per coalesced store. Entries of one word from different visits hold
+// disjoint reached bits, so the order does not matter. An entry whose first
+// cell lies outside the grid is skipped (defensive; the kernel never writes
+// one).
+__device__ __forceinline__ uint32_t spread_nibble(uint32_t n) {   // bit i -> bit 8 i
+    return (n * 0x204081u) & 0x01010101u;
+}
+
 template <typename DT>
 __global__ void __launch_bounds__(256) k_log_decode(const uint32_t *log, const uint32_t *fill,
                                                     const Ctl *ctl, uint32_t chunks, void *dist,
                                                     uint32_t ncells, uint32_t *err) {
-    __shared__ uint32_t sv[8][32][33];
+    __shared__ uint32_t sb[8][32][9];   // per warp: 32 entries x 8 words of 4 byte offsets (+ pad)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t used = min(ctl->log_next, chunks);
     for (uint32_t c = blockIdx.x; c < used; c += gridDim.x) {
@@ -244,23 +252,23 @@ __global__ void __launch_bounds__(256) k_log_decode(const uint32_t *log, const u
                 for (int b = 0; b < 5; ++b) pl[b] = base[(3 + b) * kLogChunk + e];
             }
             if (cell0 >= ncells) nb = 0u;
-#pragma unroll 4
-            for (int x = 0; x < 32; ++x) {
-                uint32_t off = 0u;
 #pragma unroll
-                for (int b = 0; b < 5; ++b) off |= ((pl[b] >> x) & 1u) << b;
-                off ^= off >> 1;
-                off ^= off >> 2;
-                off ^= off >> 4;
-                sv[warp][lane][x] = lay + off;
+            for (int b = 3; b >= 0; --b) pl[b] ^= pl[b + 1];   // Gray -> binary, bit-sliced
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                uint32_t off4 = 0u;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) off4 += spread_nibble((pl[b] >> (4 * q)) & 0xfu) << b;
+                sb[warp][lane][q] = off4;
             }
             __syncwarp();
             const uint32_t m = min(32u, n - g);
             for (uint32_t j = 0; j < m; ++j) {
                 const uint32_t c0 = __shfl_sync(0xffffffffu, cell0, (int)j);
                 const uint32_t bj = __shfl_sync(0xffffffffu, nb, (int)j);
+                const uint32_t lj = __shfl_sync(0xffffffffu, lay, (int)j);
                 if ((bj >> lane) & 1u) {
-                    const uint32_t layer = sv[warp][j][lane];
+                    const uint32_t layer = lj + ((sb[warp][j][lane >> 2] >> (8 * (lane & 3))) & 0xffu);
                     if (sizeof(DT) == 2 && layer > 0xfffeu) atomicOr(err, ERR_OVERFLOW);
                     else reinterpret_cast<DT *>(dist)[c0 + (uint32_t)lane] = (DT)layer;
                 }

@@ -144,7 +144,8 @@ def kernel_source_hash() -> str:
 
 
 def measured_traffic(workload: str, variant: int, depth: int):
-    """DRAM bytes per k_propagate launch from the committed ncu capture, or
+    """DRAM bytes per propagation (k_propagate + k_log_decode launch) from the
+    committed ncu capture, or
     None when the kernel sources changed since it was taken, or the capture
     was of another workload or tiling."""
     try:
@@ -420,13 +421,15 @@ def main():
         pg.barrier()
     prop_avg = sum(prop_ms) / len(prop_ms)
 
-    # roofline of the dominant kernel (the persistent propagation kernel)
+    # roofline of the dominant kernel: the persistent propagation kernel and
+    # the activation-log decode that completes its distance plane (the
+    # context's propagate events bracket both)
     peak, peak_kind = peaks()
     achieved = units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": measured_traffic(w.name, st["variant"], st["depth"]),
             "peak_kind": peak_kind,
-            "kernel": "k_propagate", "ms_per_launch": prop_avg,
+            "kernel": "k_propagate + k_log_decode", "ms_per_launch": prop_avg,
             "note": "algorithmic bytes = 8.125 B per effective cell-update (mask bit + uint32 "
                     "read + write per layer); temporal blocking does each update in registers"}
 

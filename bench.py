@@ -59,6 +59,9 @@ def parse():
                     help="mazes timed with one launch per layer (the slow baseline)")
     ap.add_argument("--fig5", action="store_true",
                     help="the paper's run-time experiment on empty n x n grids with fixed L")
+    ap.add_argument("--table1", action="store_true",
+                    help="one launch per layer (the paper's recursive mode) vs the persistent "
+                         "kernel on a 2000 x 2000 grid and on the 1024 x 1024 maze")
     return ap.parse_args()
 
 
@@ -212,10 +215,25 @@ def time_oracle(w, reps=1):
 def cpu_baseline(w, sample_side=23170):
     s = crop(w, sample_side) if sample_side < w.H else w
     dt, L = time_oracle(s)
-    return {"value": s.H * s.W * L / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"top-left {s.H}x{s.W} window of the workload with the {s.targets.size} targets "
-                      f"and {s.starts.size} starts inside it (L={L}); single-thread BFS + trace, "
-                      f"{dt:.1f} s", "seconds": dt, "host_cores": os.cpu_count()}
+    out = {"value": s.H * s.W * L / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"top-left {s.H}x{s.W} window of the workload with the {s.targets.size} targets "
+                     f"and {s.starts.size} starts inside it (L={L}); single-thread BFS + trace, "
+                     f"{dt:.1f} s", "seconds": dt, "host_cores": os.cpu_count()}
+    # the parallel CPU baseline (level-synchronous BFS on all host cores),
+    # median of three runs, its distances checked against the oracle's
+    import oracle
+    want, _ = oracle.bfs(s.mask, s.targets)
+    runs, same, threads, Lp = [], True, 0, 0
+    for _ in range(3):
+        t0 = time.perf_counter()
+        d, Lp, threads = oracle.bfs_parallel(s.mask, s.targets)
+        runs.append(time.perf_counter() - t0)
+        same = same and Lp == L and bool(np.array_equal(d, want))
+    tp = statistics.median(runs)
+    out["parallel"] = {"value": s.H * s.W * Lp / tp, "unit": UNIT, "cores": threads,
+                       "kind": "openmp level-synchronous BFS (no trace)", "seconds": tp,
+                       "equals_oracle": same}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -336,6 +354,40 @@ def run_fig5(args):
     return 0
 
 
+def run_table1(args):
+    """The paper's Appendix Table I comparison: the recursive mode (one launch
+    per layer, a convergence check on the host every 64 layers) against the
+    persistent kernel, on a 2000 x 2000 grid (Bernoulli 0.25, 16 targets) and
+    on the 1024 x 1024 DFS maze; device-resident inputs, propagation only."""
+    import torch
+    import paper_2004_00540_gb300 as pkg
+    w2 = synth.c5_huge(side=2000)
+    cases = [("grid2000_bernoulli0.25_rect10", w2.mask, w2.targets[:16]),
+             ("maze1024_dfs", synth.c2_maze().mask, synth.c2_maze().targets)]
+    rows = []
+    for name, mask, targets in cases:
+        m = torch.from_numpy(mask).cuda()
+        t = torch.from_numpy(np.ascontiguousarray(targets).view(np.int32)).cuda()
+        with pkg.Planner(m, pkg.MPN_DIST_U32) as pl:
+            pl.propagate(t)
+            L = pl.layers
+            pers = []
+            for _ in range(3):
+                pl.propagate(t)
+                pers.append(pl.stats()["ms_propagate"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pl.propagate(t, plain=True, check_every=64)
+            torch.cuda.synchronize()
+            plain_ms = (time.perf_counter() - t0) * 1e3
+            assert pl.layers == L
+        p_ms = min(pers)
+        rows.append({"case": name, "layers": L, "persistent_ms": p_ms, "per_layer_launches_ms": plain_ms,
+                     "ratio": plain_ms / p_ms})
+    print(json.dumps({"table1_recursive_vs_persistent": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -343,6 +395,8 @@ def main():
         return run_reference(args, rank, world)
     if args.fig5:
         return run_fig5(args)
+    if args.table1:
+        return run_table1(args)
 
     import torch
     import paper_2004_00540_gb300 as pkg
@@ -426,8 +480,10 @@ def main():
     # context's propagate events bracket both)
     peak, peak_kind = peaks()
     achieved = units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / 1e9
+    traffic = measured_traffic(w.name, st["variant"], st["depth"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": measured_traffic(w.name, st["variant"], st["depth"]),
+            "frac": achieved / peak, "traffic": traffic,
+            "dram_frac": (traffic / (prop_avg * 1e-3) / (peak * 1e9)) if traffic else None,
             "peak_kind": peak_kind,
             "kernel": "k_propagate + k_log_decode", "ms_per_launch": prop_avg,
             "note": "algorithmic bytes = 8.125 B per effective cell-update (mask bit + uint32 "
@@ -484,7 +540,12 @@ def main():
         "propagate": {"ms": prop_avg, "effective_cell_updates_per_s": units / (prop_avg * 1e-3),
                       "pct_hbm_roofline": 100 * units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / (peak * 1e9),
                       "sweeps": st["sweeps"], "tile_visits": st["tile_visits"],
-                      "tiles": st["tiles_x"] * st["tiles_y"], "blocks": st["blocks"]},
+                      "tiles": st["tiles_x"] * st["tiles_y"], "blocks": st["blocks"],
+                      "tile_layers_executed_frac": st["tile_layers"] / max(1, st["tile_visits"] * st["depth"]),
+                      "log_entries": st["log_entries"]},
+        "trace": {"ms": st["ms_trace"], "paths": int(n), "cells": total,
+                  "paths_per_s": n / (st["ms_trace"] * 1e-3) if st["ms_trace"] else None,
+                  "cells_per_s": total / (st["ms_trace"] * 1e-3) if st["ms_trace"] else None},
         "roofline": roof,
         "gpu_launches": int(launches),
         "clocks": clk,

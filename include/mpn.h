@@ -227,6 +227,11 @@ typedef struct {
     uint32_t sweeps;                 /* grid-wide rounds of the last propagate */
     uint64_t tile_visits;            /* tile visits of the last propagate */
     float ms_encode, ms_propagate, ms_trace;   /* device time of the last call of each */
+    uint64_t tile_layers;            /* layers those tile visits ran: a visit stops early once
+                                        its region is stable, so tile_layers / (tile_visits *
+                                        depth) is the fraction of tile-layers executed */
+    uint64_t log_entries;            /* activation-log entries (one per word and visit that
+                                        reached cells in it) the last propagate wrote */
 } mpn_stats;
 
 /* Statistics of the last calls (waits for the GPU). */

@@ -67,6 +67,36 @@ def _lib():
     return _lib_handle
 
 
+_PAR_SO = os.path.join(_HERE, "libparbfs.so")
+_PAR_SRC = os.path.join(_HERE, "parallel_bfs.c")
+_par_handle = None
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile parallel_bfs.c (the OpenMP CPU baseline, not the oracle)."""
+    if force or not os.path.exists(_PAR_SO) or os.path.getmtime(_PAR_SO) < os.path.getmtime(_PAR_SRC):
+        tmp = _PAR_SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _PAR_SRC,
+                               "-o", tmp])
+        os.replace(tmp, _PAR_SO)
+    return _PAR_SO
+
+
+def _par_lib():
+    global _par_handle
+    with _lock:
+        if _par_handle is None:
+            build_parallel()
+            L = ctypes.CDLL(_PAR_SO)
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            L.parallel_bfs.argtypes = [ctypes.POINTER(ctypes.c_uint8), ctypes.c_int64, ctypes.c_int64,
+                                       u32p, ctypes.c_int64, u32p, u32p,
+                                       ctypes.POINTER(ctypes.c_int32)]
+            L.parallel_bfs.restype = ctypes.c_int
+            _par_handle = L
+    return _par_handle
+
+
 def _p(a: np.ndarray, t):
     return a.ctypes.data_as(ctypes.POINTER(t))
 
@@ -91,6 +121,22 @@ def bfs(mask, targets, max_layers: int = 0):
     if st:
         raise OracleError(st, "oracle_bfs")
     return dist, int(layers.value)
+
+
+def bfs_parallel(mask, targets):
+    """The parallel CPU baseline (level-synchronous BFS on all host cores,
+    parallel_bfs.c; not the oracle): distances, layers and the threads used."""
+    m = _mask(mask)
+    H, W = m.shape
+    t = np.ascontiguousarray(targets, np.uint32)
+    dist = np.empty((H, W), np.uint32)
+    layers = ctypes.c_uint32(0)
+    threads = ctypes.c_int32(0)
+    st = _par_lib().parallel_bfs(_p(m, ctypes.c_uint8), H, W, _p(t, ctypes.c_uint32), t.size,
+                                 _p(dist, ctypes.c_uint32), ctypes.byref(layers), ctypes.byref(threads))
+    if st:
+        raise OracleError(st, "parallel_bfs")
+    return dist, int(layers.value), int(threads.value)
 
 
 def trace(mask, dist, starts):

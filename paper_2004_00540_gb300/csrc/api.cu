@@ -727,6 +727,8 @@ mpn_status mpn_get_stats(mpn_ctx *c, mpn_stats *out) {
     out->layers = c->last_layers;
     out->sweeps = c->last_ctl.sweeps;
     out->tile_visits = c->last_ctl.visits;
+    out->tile_layers = c->last_ctl.tile_layers;
+    out->log_entries = c->last_ctl.log_entries;
     // timings are best effort: a failed query leaves the last value and no
     // stale error behind for the next launch check
     if (c->ev_enc && cudaEventElapsedTime(&c->ms_encode, c->ev[0], c->ev[1]) != cudaSuccess)

@@ -34,6 +34,8 @@ struct Ctl {
     unsigned int sweeps;
     unsigned int plain_last;       // per-layer kernel: last layer that activated a cell
     unsigned long long visits;     // tile visits
+    unsigned long long tile_layers;   // layers those visits ran (a stable region stops early)
+    unsigned long long log_entries;   // activation-log entries written
 };
 
 // Bit planes and distance plane of one grid. Bit b of word w in row y is cell

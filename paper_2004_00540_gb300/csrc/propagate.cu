@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     Ctl *ctl = p.ctl;
     unsigned thr_maxl = 0u;              // largest layer this thread's words reached
     unsigned long long blk_visits = 0;   // thread 0: tile visits of this block
+    unsigned long long blk_layers = 0;   // thread 0: layers those visits ran
     unsigned vq = 0u;                    // visit parity (block-uniform)
     bool log_more = p.log != nullptr;    // thread 0: the pool may still have chunks
     const uint32_t maxv = (uint32_t)(p.TY * p.TXW);   // log entries one visit can need
@@ -149,7 +150,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                 s_mask[vq] = 0u;   // last read two visits ago, before the previous visit's first barrier
                 if (log_more && (s_chunk < 0 || s_cursor + maxv > kLogChunk)) {
                     // this chunk may not hold the visit's entries: take the next one
-                    if (s_chunk >= 0) p.log_fill[s_chunk] = s_cursor;
+                    if (s_chunk >= 0) {
+                        p.log_fill[s_chunk] = s_cursor;
+                        atomicAdd(&ctl->log_entries, (unsigned long long)s_cursor);
+                    }
                     const uint32_t c = atomicAdd(&ctl->log_next, 1u);
                     log_more = c < p.log_chunks;
                     s_chunk = log_more ? (int)c : -1;
@@ -159,8 +163,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             v.ty = t / p.ntx;
             v.tx = t - v.ty * p.ntx;
             uint32_t fmask;
-            unsigned lastj;
-            wave::visit_tile<RXW, R, NW>(v, sm, &ctl->err, &fmask, &lastj, lg);
+            unsigned lastj, jrun = 0;
+            wave::visit_tile<RXW, R, NW>(v, sm, &ctl->err, &fmask, &lastj, lg, &jrun);
             uint32_t pend_i = 0u;
             const bool pend_new = pend_t >= 0 && pend_old < stamp;   // previous visit's push
             if (pend_new) pend_i = atomicAdd(&ctl->list_len[slot1], 1u);
@@ -168,6 +172,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             if (lastj) thr_maxl = max(thr_maxl, l0 + lastj);
             if (threadIdx.x == 0) {
                 ++blk_visits;
+                blk_layers += jrun;
                 s_tile = (next_i < len) ? (int)ld_relaxed(list + next_i) : -1;
             }
             __syncthreads();
@@ -199,7 +204,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                 done = 1;
             }
             if (done && blockIdx.x == 0) ctl->sweeps = s + 1;
-            if (done && blk_visits) atomicAdd(&ctl->visits, blk_visits);
+            if (done && blk_visits) {
+                atomicAdd(&ctl->visits, blk_visits);
+                atomicAdd(&ctl->tile_layers, blk_layers);
+            }
             s_done = done;
             s_maxl = 0u;
             s_len = nlen;
@@ -210,7 +218,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             if (thr_maxl) atomicMax(&s_maxl, thr_maxl);
             __syncthreads();
             if (threadIdx.x == 0 && s_maxl) atomicMax(&ctl->max_layer, s_maxl);
-            if (threadIdx.x == 0 && s_chunk >= 0) p.log_fill[s_chunk] = s_cursor;
+            if (threadIdx.x == 0 && s_chunk >= 0) {
+                p.log_fill[s_chunk] = s_cursor;
+                atomicAdd(&ctl->log_entries, (unsigned long long)s_cursor);
+            }
             return;
         }
     }

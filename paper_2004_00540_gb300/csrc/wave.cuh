@@ -214,7 +214,8 @@ template <int RXW, int R, int NW, bool NAMED>
 __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
                                            uint32_t (&V)[R], const uint32_t (&F)[R],
                                            const uint32_t (&OWN)[R], uint32_t *fmask_out,
-                                           unsigned *lastj_out, const LogSink &lg = LogSink()) {
+                                           unsigned *lastj_out, const LogSink &lg = LogSink(),
+                                           unsigned *jrun_out = nullptr) {
     constexpr int GPW = 32 / RXW;
     constexpr int G = NW * GPW;
     constexpr int NBAR = NW * 32;
@@ -290,8 +291,12 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     };
     // unreached cells: gray(j - 1) -> gray(j), plane ctz(j)
 #define MPN_FLIP(B) _Pragma("unroll") for (int i = 0; i < R; ++i) P[B][i] ^= ~V[i]
+    int jdone = v.jmax;   // layers run (fewer when the region turns stable)
     for (int j = 1; j <= v.jmax; j += 4) {   // j = 1 mod 4
-        if (!layer(sm.xtop[1], sm.xbot[1], Check())) break;
+        if (!layer(sm.xtop[1], sm.xbot[1], Check())) {
+            jdone = j - 1;
+            break;
+        }
         if (j == v.jmax) break;
         MPN_FLIP(0);
         if (!layer(sm.xtop[0], sm.xbot[0], Plain())) break;
@@ -309,6 +314,7 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
         }
     }
 #undef MPN_FLIP
+    if (jrun_out) *jrun_out = (unsigned)jdone;
 
     // cells of this tile's interior first reached in this visit
     uint32_t NB[R];
@@ -437,7 +443,8 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
 template <int RXW, int R, int NW>
 __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
                                            uint32_t *fmask_out, unsigned *lastj_out,
-                                           const LogSink &lg = LogSink()) {
+                                           const LogSink &lg = LogSink(),
+                                           unsigned *jrun_out = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int w = lane % RXW;
     const int g = row_group<RXW, NW>(warp, lane);
@@ -460,7 +467,7 @@ __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &s
         const uint64_t vn = in ? ld_pair(gd.state + 4 * off + 2 * v.par) : 0ull;
         V[i] = (uint32_t)vn & (own ? 0xffffffffu : ~(uint32_t)(vn >> 32));
     }
-    visit_core<RXW, R, NW, false>(v, sm, err, V, F, OWN, fmask_out, lastj_out, lg);
+    visit_core<RXW, R, NW, false>(v, sm, err, V, F, OWN, fmask_out, lastj_out, lg, jrun_out);
 }
 
 }  // namespace wave

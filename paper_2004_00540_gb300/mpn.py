@@ -52,6 +52,7 @@ class mpn_stats(ctypes.Structure):
         ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("blocks", ctypes.c_int32),
         ("layers", ctypes.c_uint32), ("sweeps", ctypes.c_uint32), ("tile_visits", ctypes.c_uint64),
         ("ms_encode", ctypes.c_float), ("ms_propagate", ctypes.c_float), ("ms_trace", ctypes.c_float),
+        ("tile_layers", ctypes.c_uint64), ("log_entries", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

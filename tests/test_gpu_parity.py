@@ -231,6 +231,28 @@ def test_workload_c5_huge_full():
     w = synth.c5_huge()
     stats = assert_parity(w.mask, w.targets, w.starts)
     assert stats["layers"] > 100
+    # the activation log carried the distances (one entry per word and
+    # visit that reached cells in it), and visits stopped early where stable
+    assert stats["log_entries"] > 0
+    assert stats["tile_visits"] <= stats["tile_layers"] <= stats["tile_visits"] * stats["depth"]
+
+
+def test_activation_log_counts_match_the_oracle():
+    """Every entry is one (word, sweep) pair in which the word gained cells:
+    with one visit per tile and sweep, their number is the count of distinct
+    (32-cell word, sweep of k layers) pairs among the cells the oracle
+    reaches at distance >= 1."""
+    m, t, s = rand_case(700, 900, 0.28, 5, 10, 91)
+    with pkg.Planner(m) as pl:
+        pl.set_tuning(0, 16)
+        pl.propagate(t)
+        st = pl.stats()
+    d, _ = oracle.bfs(m, t)
+    H, W = d.shape
+    ys, xs = np.nonzero((d != oracle.INF) & (d >= 1))
+    sweep = (d[ys, xs].astype(np.int64) - 1) // 16
+    pairs = np.unique((ys.astype(np.int64) * ((W + 31) // 32) + xs // 32) * 100000 + sweep)
+    assert st["log_entries"] == pairs.size
 
 
 def test_autotune_records_choice_and_stays_exact():

@@ -311,3 +311,36 @@ def test_euclid_diagonal_and_validity():
             ay, ax = divmod(int(a), 60)
             by, bx = divmod(int(b), 60)
             assert max(abs(ay - by), abs(ax - bx)) == 1 and not m[by, bx]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_parallel_cpu_baseline_equals_oracle(seed):
+    """The OpenMP level-synchronous BFS (the parallel CPU baseline, not the
+    oracle) gives the oracle's distances and layer count."""
+    rng = np.random.default_rng(100 + seed)
+    H, W = (int(v) for v in rng.integers(1, 400, 2))
+    kind = seed % 3
+    if kind == 0:
+        m = synth.bernoulli(H, W, 0.3, 200 + seed)
+    elif kind == 1:
+        m = synth.dfs_maze(max(H, 3), max(W, 3), 300 + seed)
+        H, W = m.shape
+    else:
+        m = synth.empty(H, W)
+    free = np.flatnonzero(m.reshape(-1) == 0)
+    t = rng.choice(free, min(free.size, 1 + seed), replace=False).astype(np.uint32)
+    d1, l1 = oracle.bfs(m, t)
+    d2, l2, threads = oracle.bfs_parallel(m, t)
+    assert threads >= 1
+    assert l1 == l2 and np.array_equal(d1, d2)
+
+
+def test_parallel_cpu_baseline_errors():
+    m = synth.empty(5, 5)
+    m[2, 2] = 1
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.bfs_parallel(m, np.array([12], np.uint32))
+    assert e.value.code == oracle.EOBSTACLE
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.bfs_parallel(m, np.array([25], np.uint32))
+    assert e.value.code == oracle.EINVAL

@@ -312,6 +312,13 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running,
 /* *state = MPN_BATCH_PENDING / _DONE / _FAILED (then returns its error). */
 mpn_status mpn_batch_poll(mpn_batch *b, uint64_t ticket, int32_t *state);
 
+/* Run rounds of max_sweeps sweeps (0: to convergence) until grid `ticket`
+ * is DONE or FAILED; *state as in mpn_batch_poll (may be NULL). Other grids
+ * advance with it. Returns the grid's status like mpn_batch_poll, an error of
+ * a round, or MPN_ETIMEOUT after 2^20 rounds without an outcome. (The paper's
+ * one-shot network has no batch; this is the blocking form of run + poll.) */
+mpn_status mpn_batch_wait(mpn_batch *b, uint64_t ticket, uint32_t max_sweeps, int32_t *state);
+
 /* Results of a DONE grid (any pointer may be NULL; host or device):
  * dist H*W of its dtype, offsets[n_starts+1], cells[offsets[n]] (MPN_ENOMEM if
  * cells_cap is smaller), status[n_starts], *layers. */

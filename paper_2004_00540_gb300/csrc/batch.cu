@@ -861,6 +861,26 @@ mpn_status mpn_batch_poll(mpn_batch *b, uint64_t ticket, int32_t *state) {
     return s == MState::Failed ? it->second.code : MPN_OK;
 }
 
+mpn_status mpn_batch_wait(mpn_batch *b, uint64_t ticket, uint32_t max_sweeps, int32_t *state) {
+    if (!b) return MPN_EINVAL;
+    int32_t s = MPN_BATCH_PENDING;
+    for (uint32_t round = 0; round < (1u << 20); ++round) {
+        const mpn_status ps = mpn_batch_poll(b, ticket, &s);
+        if (s != MPN_BATCH_PENDING || (ps != MPN_OK && s != MPN_BATCH_FAILED)) {
+            if (state) *state = s;
+            return ps;
+        }
+        int32_t running = 0, done = 0;
+        const mpn_status rs = mpn_batch_run(b, max_sweeps, &running, &done);
+        if (rs != MPN_OK) {
+            if (state) *state = s;
+            return rs;
+        }
+    }
+    if (state) *state = s;
+    return MPN_ETIMEOUT;
+}
+
 mpn_status mpn_batch_result(mpn_batch *b, uint64_t ticket, void *dist, uint64_t *offsets,
                             uint32_t *cells, uint64_t cells_cap, int8_t *status, uint32_t *layers) {
     if (!b) return MPN_EINVAL;

@@ -29,7 +29,7 @@ EXPORTS = (
     "mpn_trace", "mpn_sync", "mpn_destroy", "mpn_status_str", "mpn_set_tuning",
     "mpn_variant_info", "mpn_get_stats", "mpn_launch_count", "mpn_propagate_noalloc",
     "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_submit", "mpn_batch_run",
-    "mpn_batch_poll", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
+    "mpn_batch_poll", "mpn_batch_wait", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
     "mpn_batch_stats", "mpn_batch_destroy", "mpn_autotune", "mpn_trace_euclid",
     "mpn_nearest_targets", "mpn_last_error",
 )
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
                                   ctypes.POINTER(u64)], ctypes.c_int),
             "mpn_batch_run": ([vp, u32, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
             "mpn_batch_poll": ([vp, u64, ctypes.POINTER(i32)], ctypes.c_int),
+            "mpn_batch_wait": ([vp, u64, u32, ctypes.POINTER(i32)], ctypes.c_int),
             "mpn_batch_result": ([vp, u64, vp, vp, vp, u64, vp, ctypes.POINTER(u32)], ctypes.c_int),
             "mpn_batch_info": ([vp, u64, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                 ctypes.POINTER(i32), ctypes.POINTER(u64)], ctypes.c_int),
@@ -481,6 +482,15 @@ class Batch:
         if s.value == MPN_BATCH_FAILED:
             return MPN_BATCH_FAILED
         _check(st, "mpn_batch_poll")
+        return s.value
+
+    def wait(self, ticket: int, max_sweeps: int = 0) -> int:
+        """Run rounds until grid `ticket` is done or failed; its state."""
+        s = ctypes.c_int32(0)
+        st = load().mpn_batch_wait(self.h, ticket, max_sweeps, ctypes.byref(s))
+        if s.value == MPN_BATCH_FAILED:
+            return MPN_BATCH_FAILED
+        _check(st, "mpn_batch_wait")
         return s.value
 
     def error(self, ticket: int) -> int:

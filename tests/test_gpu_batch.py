@@ -41,6 +41,19 @@ def test_batch_all_at_once():
         assert b.stats()["arena_used"] == 0
 
 
+def test_batch_wait_runs_rounds_until_done():
+    ws = small_members(6, side_hi=260, base_seed=60)
+    with pkg.Batch(1 << 30) as b:
+        tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
+        # short rounds: the wait takes several of them; the others advance too
+        assert b.wait(tks[3], 2) == pkg.MPN_BATCH_DONE
+        assert b.stats()["rounds"] > 1
+        check(b, tks[3], ws[3])
+        for tk, w in zip(tks, ws):
+            assert b.wait(tk) == pkg.MPN_BATCH_DONE
+            check(b, tk, w)
+
+
 def test_batch_continuous_arrivals_and_short_rounds():
     ws = small_members(30, side_hi=400, base_seed=40)
     rng = np.random.default_rng(1)

@@ -277,7 +277,9 @@ mpn_status encode_mask(mpn_ctx *c, const uint8_t *mask) {
         MPN_TRY(cudaMemcpyAsync(c->mask_stage.p, mask, n, cudaMemcpyHostToDevice, c->stream));
         dm = (const uint8_t *)c->mask_stage.p;
     }
-    MPN_TRY(launch_pack(dm, c->H, c->W, c->P, (uint32_t *)c->free_bits.p, c->stream));
+    // the propagation state is scratch here: every propagate clears it first
+    MPN_TRY(launch_pack_fast(dm, c->H, c->W, c->P, (uint32_t *)c->free_bits.p, (uint32_t *)c->state.p,
+                             c->state.bytes / sizeof(uint32_t), c->stream));
     MPN_TRY(cudaEventRecord(c->ev[1], c->stream));
     c->ev_enc = true;
     c->propagated = false;

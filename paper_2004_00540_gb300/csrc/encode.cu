@@ -41,6 +41,60 @@ __global__ void k_pack(const uint8_t *__restrict__ mask, int H, int W, int P,
     }
 }
 
+// Fast path, pass 1: the mask as one flat byte stream (no row structure, so
+// every load is an aligned 16-byte vector), packed into a flat bit stream:
+// bit f of flat word f / 32 is cell f (row-major), 1 = free; bits past the
+// last cell are 0. A lane turns 16 bytes into 16 bits (a byte compare per
+// four bytes, the four compare MSBs gathered with one multiply), two lanes
+// make a word. Needs a 16-byte-aligned mask.
+__global__ void k_pack_flat(const uint8_t *__restrict__ mask, size_t n, uint32_t *__restrict__ flat) {
+    const int lane = threadIdx.x & 31;
+    const size_t nwords = (n + 31) / 32;
+    const size_t chunks = (n + 511) / 512;   // 512 cells per warp and step
+    const size_t warps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    for (size_t c = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += warps) {
+        const size_t b0 = c * 512 + (size_t)lane * 16;
+        uint32_t m16 = 0u;
+        if (b0 + 16 <= n) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(mask + b0));
+            const uint32_t q[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t f = __vcmpeq4(q[k], 0u) & 0x80808080u;   // 0x80 per zero byte
+                m16 |= ((f * 0x00204081u) >> 28) << (4 * k);
+            }
+        } else {
+            for (int k = 0; k < 16; ++k)
+                if (b0 + k < n && mask[b0 + k] == 0) m16 |= 1u << k;
+        }
+        const uint32_t hi = __shfl_down_sync(0xffffffffu, m16, 1);
+        const size_t wi = c * 16 + (size_t)(lane >> 1);
+        if (!(lane & 1) && wi < nwords) flat[wi] = m16 | (hi << 16);
+    }
+}
+
+// Fast path, pass 2: each word of the pitched plane is a 32-bit window of the
+// flat bit stream starting at bit y * W + 32 * w (a funnel shift of two flat
+// words); bits at x >= W and words past the row are 0.
+__global__ void k_pack_rows(const uint32_t *__restrict__ flat, size_t nwords, int H, int W, int P,
+                            uint32_t *__restrict__ out) {
+    const size_t total = (size_t)H * P;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(i / P), w = (int)(i % P);
+        uint32_t v = 0u;
+        const int rem = W - w * 32;
+        if (rem > 0) {
+            const size_t b = (size_t)y * W + (size_t)w * 32;
+            const size_t k = b >> 5;
+            const uint32_t lo = flat[k], hi = (k + 1 < nwords) ? flat[k + 1] : 0u;
+            v = __funnelshift_r(lo, hi, (uint32_t)(b & 31));
+            if (rem < 32) v &= (1u << rem) - 1u;
+        }
+        out[i] = v;
+    }
+}
+
 // Copy a caller's packed free-cell plane (any pitch) into the context's
 // layout, clearing bits at x >= W and words past the row.
 __global__ void k_repack(const uint32_t *__restrict__ src, int H, int W, int sp, int P,
@@ -73,6 +127,20 @@ cudaError_t launch_pack(const uint8_t *mask, int H, int W, int P, uint32_t *free
     const size_t items = (size_t)H * ((P + kWordsPerWarp - 1) / kWordsPerWarp);
     count_launch();
     k_pack<<<grid_for(items, 8), 256, 0, st>>>(mask, H, W, P, free_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_fast(const uint8_t *mask, int H, int W, int P, uint32_t *free_bits,
+                             uint32_t *scratch, size_t scratch_words, cudaStream_t st) {
+    const size_t n = (size_t)H * W;
+    const size_t nwords = (n + 31) / 32;
+    if (((uintptr_t)mask & 15u) || !scratch || scratch_words < nwords)
+        return launch_pack(mask, H, W, P, free_bits, st);
+    count_launch(2);
+    k_pack_flat<<<grid_for((n + 511) / 512, 8), 256, 0, st>>>(mask, n, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_pack_rows<<<grid_for((size_t)H * P, 256), 256, 0, st>>>(scratch, nwords, H, W, P, free_bits);
     return cudaGetLastError();
 }
 

@@ -118,6 +118,11 @@ cudaError_t launch_plain_seed(const uint32_t *targets, int n, const GridDev &g, 
 
 cudaError_t launch_pack(const uint8_t *mask, int H, int W, int P, uint32_t *free_bits,
                         cudaStream_t st);
+// launch_pack through a flat bit stream in `scratch` (at least H * W / 32 + 1
+// words; clobbered): vector loads, for a 16-byte-aligned mask (otherwise it is
+// launch_pack).
+cudaError_t launch_pack_fast(const uint8_t *mask, int H, int W, int P, uint32_t *free_bits,
+                             uint32_t *scratch, size_t scratch_words, cudaStream_t st);
 cudaError_t launch_repack(const uint32_t *src, int H, int W, int src_pitch, int P,
                           uint32_t *free_bits, cudaStream_t st);
 

@@ -131,8 +131,15 @@ __global__ void __launch_bounds__(kTraceWarps * 32)
     uint32_t d = (uint32_t)dist[c];
     const uint32_t d0 = d;
     if (CELLS && lane == 0) cells[o] = c;
+    int ddy = 0, ddx = 0;   // how far the walk moved in the last window
     while (d > 0) {
-        const int wy0 = cy - kWin / 2, wx0 = cx - kWin / 2;
+        // the next window reaches further in the direction the walk has been
+        // heading: along an axis on which it moved at least kWin / 4 cells in
+        // the last window, the current cell sits a quarter window in from the
+        // trailing edge; otherwise it is centred
+        const int oy = ddy >= kWin / 4 ? kWin / 4 : (ddy <= -kWin / 4 ? kWin - 1 - kWin / 4 : kWin / 2);
+        const int ox = ddx >= kWin / 4 ? kWin / 4 : (ddx <= -kWin / 4 ? kWin - 1 - kWin / 4 : kWin / 2);
+        const int wy0 = cy - oy, wx0 = cx - ox;
         const int x = wx0 + lane;
 #pragma unroll 8
         for (int r = 0; r < kWin; ++r) {
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(kTraceWarps * 32)
             wb[r * kWinPitch + lane] = v;
         }
         __syncwarp();
-        int ly = kWin / 2, lx = kWin / 2;
+        int ly = oy, lx = ox;
         while (d > 0 && ly >= 1 && ly <= kWin - 2 && lx >= 1 && lx <= kWin - 2) {
             bool hit = false;
             if (lane < 8) hit = (uint32_t)wb[(ly + my_dy) * kWinPitch + lx + my_dx] == d - 1u;
@@ -151,14 +158,18 @@ __global__ void __launch_bounds__(kTraceWarps * 32)
                 if (lane == 0) atomicOr(err, ERR_TRACE);
                 return;
             }
+            // neighbour q's offsets from two packed tables (2 bits per q:
+            // offset + 1), the same order as my_dy / my_dx
             const int q = __ffs(m) - 1;
-            ly += __shfl_sync(0xffffffffu, my_dy, q);
-            lx += __shfl_sync(0xffffffffu, my_dx, q);
+            ly += (int)((0xa940u >> (2 * q)) & 3u) - 1;
+            lx += (int)((0x9224u >> (2 * q)) & 3u) - 1;
             --d;
             ++o;
             if (CELLS && lane == 0) cells[o] = (uint32_t)((wy0 + ly) * g.W + (wx0 + lx));
         }
         __syncwarp();
+        ddy = ly - oy;
+        ddx = lx - ox;
         cy = wy0 + ly;
         cx = wx0 + lx;
     }

@@ -178,6 +178,26 @@ def test_device_tensors_in_and_out():
     assert np.array_equal(status.cpu().numpy(), ostatus)
 
 
+@pytest.mark.parametrize("offset", [0, 1, 8])
+def test_device_mask_at_any_alignment(offset):
+    """The encoder's vector path needs a 16-byte-aligned mask; a mask at any
+    other address takes the byte path. Both give the oracle's plane."""
+    torch = pytest.importorskip("torch")
+    m, t, s = rand_case(301, 517, 0.3, 3, 5, 70 + offset)
+    big = torch.zeros(301 * 517 + 64, dtype=torch.uint8, device="cuda")
+    big[offset:offset + 301 * 517] = torch.from_numpy(m.reshape(-1)).cuda()
+    dm = big[offset:offset + 301 * 517]
+    ctx = pkg.mpn_create(dm, 301, 517, 32, torch.cuda.current_stream())
+    try:
+        L = pkg.mpn_propagate(ctx, t)
+        d = np.empty((301, 517), np.uint32)
+        pkg.mpn_get_distances(ctx, d)
+    finally:
+        pkg.mpn_destroy(ctx)
+    od, oL = oracle.bfs(m, t)
+    assert L == oL and np.array_equal(d, od)
+
+
 def test_packed_input_and_set_mask():
     m, t, s = rand_case(130, 200, 0.3, 2, 20, 8)
     P = 8

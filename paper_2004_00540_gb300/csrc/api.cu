@@ -176,7 +176,7 @@ namespace {
 mpn_status configure(mpn_ctx *c, int variant, int depth) {
     if (variant < 0 || variant >= num_variants()) return MPN_EINVAL;
     const VariantDesc vd = variant_desc(variant);
-    const int ry = vd.nwarps * (32 / vd.rxw) * vd.r;
+    const int ry = region_rows(vd);
     // the halo (depth rows) must not reach past the neighbouring tiles: a
     // visit queues only its 8 neighbours, so the interior needs >= depth rows
     if (depth < 1 || depth > 32 || ry - 2 * depth < depth) return MPN_EINVAL;
@@ -411,7 +411,7 @@ mpn_status mpn_set_tuning(mpn_ctx *c, int32_t variant, int32_t depth) {
 mpn_status mpn_variant_info(int32_t v, int32_t *rows, int32_t *words, int32_t *threads) {
     if (v < 0 || v >= num_variants()) return MPN_EINVAL;
     const VariantDesc d = variant_desc(v);
-    if (rows) *rows = d.nwarps * (32 / d.rxw) * d.r;
+    if (rows) *rows = region_rows(d);
     if (words) *words = d.rxw;
     if (threads) *threads = variant_threads(v);
     return MPN_OK;

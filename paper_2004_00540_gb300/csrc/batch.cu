@@ -507,7 +507,7 @@ mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream
 mpn_status mpn_batch_set_depth(mpn_batch *b, int32_t depth) {
     if (!b || depth < 0 || depth > 32) return MPN_EINVAL;
     const VariantDesc vd = variant_desc(b->variant);
-    const int ry = vd.nwarps * (32 / vd.rxw) * vd.r;
+    const int ry = region_rows(vd);
     if (depth && ry - 2 * depth < depth) return MPN_EINVAL;
     b->depth_override = depth;
     return MPN_OK;
@@ -528,7 +528,7 @@ mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_
     m.dist_bits = dist_bits;
     m.k = depth_for(b, H, W);
     const VariantDesc vd = variant_desc(b->variant);
-    const int ry = vd.nwarps * (32 / vd.rxw) * vd.r;
+    const int ry = region_rows(vd);
     m.TY = ry - 2 * m.k;
     m.TXW = vd.rxw - 2;
     m.ntx = ((W + 31) / 32 + m.TXW - 1) / m.TXW;

@@ -84,12 +84,16 @@ constexpr uint32_t kLogChunk = 4096;
 constexpr uint32_t kLogFields = 8;
 
 struct VariantDesc {
-    int rxw;      // region words (lanes per row group)
+    int rxw;      // region words (lanes per row group x words per lane)
     int r;        // rows per lane
     int nwarps;   // warps per block that run the layers
     int minb;     // blocks per SM the register budget aims at
     int tma;      // 1: one more (producer) warp stages regions with TMA; uint32 planes only
+    int wpl = 1;  // adjacent words of a row per lane
 };
+
+// Rows of a variant's region: warps x row groups per warp x rows per lane.
+inline int region_rows(const VariantDesc &d) { return d.nwarps * (32 / (d.rxw / d.wpl)) * d.r; }
 
 // ---- autotuner table (api.cu): best depth per (size bucket, variant) ----
 // bucket = ceil(log2(max(H, W))); returns false when nothing was measured.

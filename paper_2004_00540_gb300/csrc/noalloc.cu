@@ -74,7 +74,7 @@ extern "C" mpn_status mpn_propagate_noalloc(const uint8_t *mask, int32_t H, int3
     const int P = (((W + 31) / 32) + 3) / 4 * 4;
     if ((size_t)H * P > kNaPlaneWords) return MPN_EINVAL;
     const VariantDesc vd = variant_desc(kNaVariant);
-    const int ry = vd.nwarps * (32 / vd.rxw) * vd.r;
+    const int ry = region_rows(vd);
     const int TY = ry - 2 * kNaDepth, TXW = vd.rxw - 2;
     const int ntx = ((W + 31) / 32 + TXW - 1) / TXW, nty = (H + TY - 1) / TY;
     const size_t ntiles = (size_t)ntx * nty;

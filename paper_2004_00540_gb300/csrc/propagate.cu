@@ -72,11 +72,11 @@ __device__ __forceinline__ int zone_tile(const PropParams &p, int ty, int tx, ui
 // visit, and append the tile to the list once the next visit's layers are
 // done, so neither atomic's round trip stands between two visits; the last
 // visit of a sweep finishes its pushes before the grid barrier.
-template <int RXW, int R, int NW, int MINB, typename DT>
+template <int RXW, int R, int NW, int MINB, typename DT, int WPL = 1>
 __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
-    static_assert(RXW == 4 || RXW == 8 || RXW == 16 || RXW == 32, "row group width");
+    static_assert(RXW == 4 || RXW == 8 || RXW == 16 || RXW == 32, "region words");
     static_assert(R >= 1, "rows per lane");
-    __shared__ wave::VisitSmem<RXW, NW> sm;
+    __shared__ wave::VisitSmem<RXW, NW, WPL> sm;
     __shared__ int s_tile;
     __shared__ unsigned s_mask[2], s_done, s_maxl, s_ok;   // s_mask by visit parity
     __shared__ uint32_t s_len;                              // length of this sweep's list
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             v.tx = t - v.ty * p.ntx;
             uint32_t fmask;
             unsigned lastj, jrun = 0;
-            wave::visit_tile<RXW, R, NW>(v, sm, &ctl->err, &fmask, &lastj, lg, &jrun);
+            wave::visit_tile<RXW, R, NW, WPL>(v, sm, &ctl->err, &fmask, &lastj, lg, &jrun);
             uint32_t pend_i = 0u;
             const bool pend_new = pend_t >= 0 && pend_old < stamp;   // previous visit's push
             if (pend_new) pend_i = atomicAdd(&ctl->list_len[slot1], 1u);
@@ -607,10 +607,10 @@ __global__ void k_plain_layer(GridDev g, uint32_t layer, Ctl *ctl) {
     if (who && (threadIdx.x & 31) == __ffs(who) - 1) atomicMax(&ctl->plain_last, layer);
 }
 
-template <int RXW, int R, int NW, int MINB>
+template <int RXW, int R, int NW, int MINB, int WPL = 1>
 void *variant_ptr(bool u16) {
-    return u16 ? (void *)k_propagate<RXW, R, NW, MINB, uint16_t>
-               : (void *)k_propagate<RXW, R, NW, MINB, uint32_t>;
+    return u16 ? (void *)k_propagate<RXW, R, NW, MINB, uint16_t, WPL>
+               : (void *)k_propagate<RXW, R, NW, MINB, uint32_t, WPL>;
 }
 
 // Compiled tile shapes: {region words, rows per lane, warps per block, blocks
@@ -627,6 +627,8 @@ constexpr VariantDesc kVariants[] = {
     {8, 4, 8, 2, 1},    // 128 rows x 256 cells, TMA-staged, + producer warp (uint32 planes)
     {8, 2, 16, 2, 0},   // 128 rows x 256 cells, 2 rows per lane (shorter per-layer chains)
     {8, 1, 32, 1, 0},   // 128 rows x 256 cells, 1 row per lane, 1024 threads
+    {8, 2, 8, 3, 0, 2},   // 128 rows x 256 cells, 2 words x 2 rows per lane
+    {8, 4, 8, 2, 0, 2},   // 256 rows x 256 cells, 2 words x 4 rows per lane
 };
 
 void *variant_fn(int v, int dist_bits) {
@@ -641,6 +643,8 @@ void *variant_fn(int v, int dist_bits) {
         case 6: return u16 ? nullptr : (void *)k_propagate_tma<8, 4, 8>;
         case 7: return variant_ptr<8, 2, 16, 2>(u16);
         case 8: return variant_ptr<8, 1, 32, 1>(u16);
+        case 9: return variant_ptr<8, 2, 8, 3, 2>(u16);
+        case 10: return variant_ptr<8, 4, 8, 2, 2>(u16);
         default: return nullptr;
     }
 }
@@ -705,7 +709,7 @@ cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int bloc
         return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(variant_threads(v)), args, 0, st);
     }
     const VariantDesc &d = kVariants[v];
-    const int ry = d.nwarps * (32 / d.rxw) * d.r, bw = (d.rxw + 6) / 4 * 4;
+    const int ry = region_rows(d), bw = (d.rxw + 6) / 4 * 4;
     CUtensorMap mf;
     cudaError_t e = plane_map(&mf, p.g.free_bits, p.g.P, p.g.H, bw, ry);
     if (e != cudaSuccess) return e;

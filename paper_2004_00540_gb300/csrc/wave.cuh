@@ -187,15 +187,31 @@ struct LogSink {
     unsigned *s_cursor = nullptr;
 };
 
-template <int RXW, int NW>
+template <int RXW, int NW, int WPL = 1>
 struct VisitSmem {
-    static constexpr int G = NW * (32 / RXW);
-    uint32_t xtop[2][NW * 32 + 1];   // per layer parity: top row of each group, dilated along the row
-    uint32_t xbot[2][NW * 32 + 1];   // bottom row; [NW * 32]: zero, the region's outer neighbours
+    // per layer parity: top row of each group, dilated along the row (WPL
+    // words per lane); past the NW * 32 lanes' slots: zero, the region's outer
+    // neighbours
+    uint32_t xtop[2][(NW * 32 + 1) * WPL];
+    uint32_t xbot[2][(NW * 32 + 1) * WPL];   // bottom row
     __device__ __forceinline__ void zero_pad() {
-        if (threadIdx.x < 4) (threadIdx.x < 2 ? xtop : xbot)[threadIdx.x & 1][NW * 32] = 0u;
+        if (threadIdx.x < 4 * WPL) {
+            const int q = threadIdx.x / WPL, u = threadIdx.x % WPL;
+            (q < 2 ? xtop : xbot)[q & 1][NW * 32 * WPL + u] = 0u;
+        }
     }
 };
+
+// 3x3 dilation along the row for a lane holding two adjacent words (a, b) of
+// a row: the carries into a come from the left lane's b and into b from the
+// right lane's a. Same edge argument as hdil.
+template <int LG>
+__device__ __forceinline__ void hdil2(uint32_t a, uint32_t b, uint32_t &ha, uint32_t &hb) {
+    const uint32_t left = __shfl_up_sync(0xffffffffu, b, 1, LG);
+    const uint32_t right = __shfl_down_sync(0xffffffffu, a, 1, LG);
+    ha = a | __funnelshift_l(left, a, 1) | __funnelshift_r(a, b, 1);
+    hb = b | __funnelshift_l(a, b, 1) | __funnelshift_r(b, right, 1);
+}
 
 // Advance one tile by up to v.jmax layers from its region already in
 // registers (V: visit bits as of the start of the sweep, F: free bits, OWN:
@@ -206,46 +222,50 @@ struct VisitSmem {
 // of this thread's cells was reached. Every participating thread calls it; it
 // contains barriers (block-wide, or named barrier 1 when NAMED).
 //
-// Block layout: a row group is RXW consecutive lanes holding RXW consecutive
-// words of R consecutive rows (one word per lane per row, in registers).
-// Region = (NW * 32 / RXW * R) rows x RXW words; interior = rows [k, RY - k)
+// Block layout: a row group is RXW / WPL consecutive lanes holding RXW
+// consecutive words of R consecutive rows (WPL adjacent words per lane per
+// row, in registers; slot s = i * WPL + u is word u of row i). Region =
+// (NW * 32 / (RXW / WPL) * R) rows x RXW words; interior = rows [k, RY - k)
 // x words [1, RXW - 1).
-template <int RXW, int R, int NW, bool NAMED>
-__device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
-                                           uint32_t (&V)[R], const uint32_t (&F)[R],
-                                           const uint32_t (&OWN)[R], uint32_t *fmask_out,
+template <int RXW, int R, int NW, bool NAMED, int WPL = 1>
+__device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WPL> &sm, uint32_t *err,
+                                           uint32_t (&V)[R * WPL], const uint32_t (&F)[R * WPL],
+                                           const uint32_t (&OWN)[R * WPL], uint32_t *fmask_out,
                                            unsigned *lastj_out, const LogSink &lg = LogSink(),
                                            unsigned *jrun_out = nullptr) {
-    constexpr int GPW = 32 / RXW;
+    static_assert(WPL == 1 || WPL == 2, "words per lane");
+    constexpr int LG = RXW / WPL;   // lanes per row group
+    constexpr int GPW = 32 / LG;
     constexpr int G = NW * GPW;
+    constexpr int S = R * WPL;      // words per thread
     constexpr int NBAR = NW * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = lane % RXW;
-    const int g = row_group<RXW, NW>(warp, lane);
+    const int wl = lane % LG;        // lane within the row group
+    const int g = row_group<LG, NW>(warp, lane);
     const int r0 = g * R;
     const int k = v.k, TY = v.TY, TXW = v.TXW;
     const GridDev &gd = v.g;
     const int y0 = v.ty * TY - k;
-    const int gw = v.tx * TXW - 1 + w;
-    const int slot = warp * 32 + lane;   // == xslot(g, w)
-    const int slot_up = g > 0 ? xslot<RXW, NW>(g - 1, w) : NW * 32;
-    const int slot_dn = g < G - 1 ? xslot<RXW, NW>(g + 1, w) : NW * 32;
-    uint32_t V0[R];   // visit bits at the start of the visit
+    const int gw0 = v.tx * TXW - 1 + wl * WPL;   // word u of a row is gw0 + u
+    const int slot = (warp * 32 + lane) * WPL;   // == xslot(g, wl) * WPL
+    const int slot_up = (g > 0 ? xslot<LG, NW>(g - 1, wl) : NW * 32) * WPL;
+    const int slot_dn = (g < G - 1 ? xslot<LG, NW>(g + 1, wl) : NW * 32) * WPL;
+    uint32_t V0[S];   // visit bits at the start of the visit
 #pragma unroll
-    for (int i = 0; i < R; ++i) V0[i] = V[i];
+    for (int s = 0; s < S; ++s) V0[s] = V[s];
 
     // ---- up to k layers in registers ----
-    // Activation times as a bit-sliced Gray-code counter: P[b][i] holds bit b
+    // Activation times as a bit-sliced Gray-code counter: P[b][s] holds bit b
     // of gray(t), t = layer - l0 - 1. Every cell not reached yet carries the
     // same count, gray(j - 1) before layer j, so advancing all of them to
     // gray(j) flips the single plane ctz(j) on the unreached cells (one
-    // operation per row and layer); a cell keeps its value once reached, and
+    // operation per word and layer); a cell keeps its value once reached, and
     // each cell's distance is written once, at the end of the visit.
-    uint32_t P[5][R];
+    uint32_t P[5][S];
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
+    for (int s = 0; s < S; ++s) {
 #pragma unroll
-        for (int b = 0; b < 5; ++b) P[b][i] = 0u;
+        for (int b = 0; b < 5; ++b) P[b][s] = 0u;
     }
     // Per layer: every row dilated along the row first (the shuffles of the
     // inner rows overlap the wait at the barrier), the group's top and bottom
@@ -266,31 +286,42 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     using Record = std::integral_constant<int, 0>;
     using Plain = std::integral_constant<int, 2>;
     auto layer = [&](uint32_t *xt, uint32_t *xb, auto kind) -> bool {
-        uint32_t h[R];
+        uint32_t h[S];
 #pragma unroll
-        for (int i = 0; i < R; ++i) h[i] = hdil<RXW>(V[i]);
-        xt[slot] = h[0];
-        xb[slot] = h[R - 1];
+        for (int i = 0; i < R; ++i) {
+            if (WPL == 1) h[i] = hdil<LG>(V[i]);
+            else hdil2<LG>(V[i * WPL], V[i * WPL + WPL - 1], h[i * WPL], h[i * WPL + WPL - 1]);
+        }
+#pragma unroll
+        for (int u = 0; u < WPL; ++u) {
+            xt[slot + u] = h[u];
+            xb[slot + u] = h[(R - 1) * WPL + u];
+        }
         if (decltype(kind)::value == Check::value) {
             if (!bar_or<NAMED, NBAR>(changed != 0u)) return false;
         } else {
             bar_sync<NAMED, NBAR>();
         }
-        const uint32_t hUp = xb[slot_up];
-        const uint32_t hDn = xt[slot_dn];
+        uint32_t hUp[WPL], hDn[WPL];
+#pragma unroll
+        for (int u = 0; u < WPL; ++u) {
+            hUp[u] = xb[slot_up + u];
+            hDn[u] = xt[slot_dn + u];
+        }
         if (decltype(kind)::value == Record::value) changed = 0u;
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const uint32_t up = (i > 0) ? h[i - 1] : hUp;
-            const uint32_t dn = (i < R - 1) ? h[i + 1] : hDn;
-            const uint32_t vn = V[i] | ((up | h[i] | dn) & F[i]);
-            if (decltype(kind)::value == Record::value) changed |= vn ^ V[i];
-            V[i] = vn;
+        for (int s = 0; s < S; ++s) {
+            const int i = s / WPL, u = s % WPL;
+            const uint32_t up = (i > 0) ? h[s - WPL] : hUp[u];
+            const uint32_t dn = (i < R - 1) ? h[s + WPL] : hDn[u];
+            const uint32_t vn = V[s] | ((up | h[s] | dn) & F[s]);
+            if (decltype(kind)::value == Record::value) changed |= vn ^ V[s];
+            V[s] = vn;
         }
         return true;
     };
     // unreached cells: gray(j - 1) -> gray(j), plane ctz(j)
-#define MPN_FLIP(B) _Pragma("unroll") for (int i = 0; i < R; ++i) P[B][i] ^= ~V[i]
+#define MPN_FLIP(B) _Pragma("unroll") for (int s = 0; s < S; ++s) P[B][s] ^= ~V[s]
     int jdone = v.jmax;   // layers run (fewer when the region turns stable)
     for (int j = 1; j <= v.jmax; j += 4) {   // j = 1 mod 4
         if (!layer(sm.xtop[1], sm.xbot[1], Check())) {
@@ -317,21 +348,21 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     if (jrun_out) *jrun_out = (unsigned)jdone;
 
     // cells of this tile's interior first reached in this visit
-    uint32_t NB[R];
+    uint32_t NB[S];
 #pragma unroll
-    for (int i = 0; i < R; ++i) NB[i] = (V[i] ^ V0[i]) & OWN[i];
+    for (int s = 0; s < S; ++s) NB[s] = (V[s] ^ V0[s]) & OWN[s];
 
     // ---- the last layer at which one of this thread's cells was reached ----
     // (a bit-sliced maximum of t over the reached cells, from the planes
     // turned from Gray code into binary, most significant bit first)
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        if (!NB[i]) continue;
+    for (int s = 0; s < S; ++s) {
+        if (!NB[s]) continue;
         uint32_t B[5];
-        B[4] = P[4][i];
+        B[4] = P[4][s];
 #pragma unroll
-        for (int b = 3; b >= 0; --b) B[b] = P[b][i] ^ B[b + 1];
-        uint32_t cand = NB[i], m = 0u;
+        for (int b = 3; b >= 0; --b) B[b] = P[b][s] ^ B[b + 1];
+        uint32_t cand = NB[s], m = 0u;
 #pragma unroll
         for (int b = 4; b >= 0; --b) {
             const uint32_t hit = cand & B[b];
@@ -348,11 +379,11 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     if (v.jmax == k) {
         const uint32_t gk = (uint32_t)(k - 1) ^ ((uint32_t)(k - 1) >> 1);   // gray(k - 1)
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            uint32_t last = NB[i];
+        for (int s = 0; s < S; ++s) {
+            uint32_t last = NB[s];
 #pragma unroll
-            for (int b = 0; b < 5; ++b) last &= ((gk >> b) & 1) ? P[b][i] : ~P[b][i];
-            fmask |= border_bits(r0 + i - k, w - 1, last, k, TY, TXW);
+            for (int b = 0; b < 5; ++b) last &= ((gk >> b) & 1) ? P[b][s] : ~P[b][s];
+            fmask |= border_bits(r0 + s / WPL - k, wl * WPL + s % WPL - 1, last, k, TY, TXW);
         }
     }
     *fmask_out = fmask;
@@ -364,49 +395,50 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
         // one activation-log entry per changed word: the warp reserves its
         // entries with one shared-memory atomic and writes them field by field
         uint32_t *base = lg.log + (size_t)chunk * (kLogFields * kLogChunk);
-        unsigned act[R];
+        unsigned act[S];
         uint32_t tot = 0u;
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            act[i] = __ballot_sync(0xffffffffu, NB[i] != 0u);
-            tot += (uint32_t)__popc(act[i]);
+        for (int s = 0; s < S; ++s) {
+            act[s] = __ballot_sync(0xffffffffu, NB[s] != 0u);
+            tot += (uint32_t)__popc(act[s]);
         }
-        uint32_t slot = 0u;
-        if (lane == 0 && tot) slot = atomicAdd(lg.s_cursor, tot);
-        slot = __shfl_sync(0xffffffffu, slot, 0);
+        uint32_t at = 0u;
+        if (lane == 0 && tot) at = atomicAdd(lg.s_cursor, tot);
+        at = __shfl_sync(0xffffffffu, at, 0);
         const unsigned below = (1u << lane) - 1u;
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            if (NB[i]) {
-                uint32_t *e = base + slot + (uint32_t)__popc(act[i] & below);
-                e[0 * kLogChunk] = (uint32_t)(y0 + r0 + i) * (uint32_t)gd.W + (uint32_t)gw * 32u;
+        for (int s = 0; s < S; ++s) {
+            if (NB[s]) {
+                uint32_t *e = base + at + (uint32_t)__popc(act[s] & below);
+                e[0 * kLogChunk] = (uint32_t)(y0 + r0 + s / WPL) * (uint32_t)gd.W +
+                                   (uint32_t)(gw0 + s % WPL) * 32u;
                 e[1 * kLogChunk] = v.l0 + 1u;
-                e[2 * kLogChunk] = NB[i];
+                e[2 * kLogChunk] = NB[s];
 #pragma unroll
-                for (int b = 0; b < 5; ++b) e[(3 + b) * kLogChunk] = P[b][i];
+                for (int b = 0; b < 5; ++b) e[(3 + b) * kLogChunk] = P[b][s];
             }
-            slot += (uint32_t)__popc(act[i]);
+            at += (uint32_t)__popc(act[s]);
         }
     } else {
     // The warp writes one changed word at a time: 32 lanes, 32 consecutive
     // cells, one coalesced store.
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        unsigned act = __ballot_sync(0xffffffffu, NB[i] != 0u);
+    for (int s = 0; s < S; ++s) {
+        unsigned act = __ballot_sync(0xffffffffu, NB[s] != 0u);
         while (act) {
             const int src = __ffs(act) - 1;
             act &= act - 1u;
-            const uint32_t nb = __shfl_sync(0xffffffffu, NB[i], src);
+            const uint32_t nb = __shfl_sync(0xffffffffu, NB[s], src);
             uint32_t off = 0u;   // gray(t) of this lane's cell, then t
 #pragma unroll
             for (int b = 0; b < 5; ++b)
-                off |= ((__shfl_sync(0xffffffffu, P[b][i], src) >> lane) & 1u) << b;
+                off |= ((__shfl_sync(0xffffffffu, P[b][s], src) >> lane) & 1u) << b;
             off ^= off >> 1;
             off ^= off >> 2;
             off ^= off >> 4;
-            const int sw = src % RXW;                 // source word column
-            const int sg = row_group<RXW, NW>(warp, src);   // source row group
-            const int y = y0 + sg * R + i;
+            const int sw = (src % LG) * WPL + s % WPL;       // source word column
+            const int sg = row_group<LG, NW>(warp, src);     // source row group
+            const int y = y0 + sg * R + s / WPL;
             const size_t cell = (size_t)y * gd.W + (size_t)(v.tx * TXW - 1 + sw) * 32 + lane;
             if ((nb >> lane) & 1u) {
                 const uint32_t layer = v.l0 + 1u + off;
@@ -425,11 +457,11 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
     // ---- publish: {V, this sweep's new bits} for this parity, {V, 0} for
     // the other (a later sweep of that parity sees no stale bits of this word)
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        if (!NB[i]) continue;
-        uint32_t *st = gd.state + 4 * ((size_t)(y0 + r0 + i) * gd.P + gw);
-        st_pair(st + 2 * v.par, V[i], NB[i]);
-        st_pair(st + 2 * (v.par ^ 1), V[i], 0u);
+    for (int s = 0; s < S; ++s) {
+        if (!NB[s]) continue;
+        uint32_t *st = gd.state + 4 * ((size_t)(y0 + r0 + s / WPL) * gd.P + gw0 + s % WPL);
+        st_pair(st + 2 * v.par, V[s], NB[s]);
+        st_pair(st + 2 * (v.par ^ 1), V[s], 0u);
     }
 }
 
@@ -440,34 +472,35 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW> &s
 // (A word last changed two or more sweeps back may still carry that sweep's
 // bits in Npar; those cells' whole neighbourhoods were reached by then, so
 // hiding them changes nothing inside the tile.)
-template <int RXW, int R, int NW>
-__device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW> &sm, uint32_t *err,
+template <int RXW, int R, int NW, int WPL = 1>
+__device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW, WPL> &sm, uint32_t *err,
                                            uint32_t *fmask_out, unsigned *lastj_out,
                                            const LogSink &lg = LogSink(),
                                            unsigned *jrun_out = nullptr) {
+    constexpr int LG = RXW / WPL;
+    constexpr int S = R * WPL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int w = lane % RXW;
-    const int g = row_group<RXW, NW>(warp, lane);
+    const int wl = lane % LG;
+    const int g = row_group<LG, NW>(warp, lane);
     const int r0 = g * R;
     const int k = v.k, TY = v.TY, TXW = v.TXW;
     const GridDev &gd = v.g;
-    const bool ownW = (w >= 1) && (w <= TXW);
     const int y0 = v.ty * TY - k;
-    const int gw = v.tx * TXW - 1 + w;
-    const bool inX = (gw >= 0) && (gw < gd.P);
-    uint32_t V[R], F[R], OWN[R];
+    const int gw0 = v.tx * TXW - 1 + wl * WPL;
+    uint32_t V[S], F[S], OWN[S];
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int rr = r0 + i, y = y0 + rr;
-        const bool in = inX && y >= 0 && y < gd.H;
-        const bool own = ownW && rr >= k && rr < k + TY;
+    for (int s = 0; s < S; ++s) {
+        const int rr = r0 + s / WPL, y = y0 + rr;
+        const int w = wl * WPL + s % WPL, gw = gw0 + s % WPL;
+        const bool in = gw >= 0 && gw < gd.P && y >= 0 && y < gd.H;
+        const bool own = w >= 1 && w <= TXW && rr >= k && rr < k + TY;
         const size_t off = (size_t)y * gd.P + gw;
-        OWN[i] = own ? 0xffffffffu : 0u;
-        F[i] = in ? __ldg(gd.free_bits + off) : 0u;
+        OWN[s] = own ? 0xffffffffu : 0u;
+        F[s] = in ? __ldg(gd.free_bits + off) : 0u;
         const uint64_t vn = in ? ld_pair(gd.state + 4 * off + 2 * v.par) : 0ull;
-        V[i] = (uint32_t)vn & (own ? 0xffffffffu : ~(uint32_t)(vn >> 32));
+        V[s] = (uint32_t)vn & (own ? 0xffffffffu : ~(uint32_t)(vn >> 32));
     }
-    visit_core<RXW, R, NW, false>(v, sm, err, V, F, OWN, fmask_out, lastj_out, lg, jrun_out);
+    visit_core<RXW, R, NW, false, WPL>(v, sm, err, V, F, OWN, fmask_out, lastj_out, lg, jrun_out);
 }
 
 }  // namespace wave

@@ -394,6 +394,13 @@ struct mpn_batch {
     uint64_t next_ticket = 1;
     uint32_t next_sweep = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // side streams for the per-grid path walks of a finished round: a walk is
+    // as long as the grid's longest path, so the grids' walks run side by
+    // side instead of one after another on the batch stream
+    static constexpr int kSide = 16;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t side_ev[kSide] = {};
+    cudaEvent_t fork_ev = nullptr;
     std::map<uint32_t, cudaGraphExec_t> graphs;   // one captured round per max_sweeps value
     bool use_graph = true;
     float last_round_ms = 0.f;
@@ -492,6 +499,11 @@ mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bc, 0, sizeof(BatchCtl), b->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    for (int i = 0; i < mpn_batch::kSide && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side_ev[i], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         mpn_batch_destroy(b);
@@ -675,7 +687,25 @@ static cudaError_t run_round(mpn_batch *b, const BatchParams &p) {
     return cudaGraphLaunch(it->second, b->stream);
 }
 
-static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t *cells) {
+// Side stream i waits for the work queued on the batch stream so far.
+static cudaError_t fork_side(mpn_batch *b) {
+    cudaError_t e = cudaEventRecord(b->fork_ev, b->stream);
+    for (int i = 0; i < mpn_batch::kSide && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->side[i], b->fork_ev, 0);
+    return e;
+}
+
+// The batch stream waits for everything queued on the side streams.
+static cudaError_t join_side(mpn_batch *b) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < mpn_batch::kSide && e == cudaSuccess; ++i) {
+        e = cudaEventRecord(b->side_ev[i], b->side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->side_ev[i], 0);
+    }
+    return e;
+}
+
+static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t *cells,
+                                      cudaStream_t st) {
     char *res = (char *)arena_at(b, m.res_off);
     GridDev g;
     g.free_bits = nullptr;
@@ -686,7 +716,7 @@ static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t 
     g.P = m.P;
     return launch_trace(g, m.dist_bits, (const uint32_t *)(res + m.st_o), m.ns,
                         (const uint64_t *)(res + m.off_o), (const int8_t *)(res + m.sts_o), cells,
-                        b->stream, &b->d_bc->c.err);
+                        st, &b->d_bc->c.err);
 }
 
 // Wait for the stream, then trace every grid that converged in the last round.
@@ -720,7 +750,10 @@ static mpn_status finish_round(mpn_batch *b) {
     // path lengths and offsets of every newly converged grid, then one wait
     Ctl *ctl = &b->d_bc->c;
     if (!done.empty()) {
+        B_TRY(fork_side(b));
+        int j = 0;
         for (HostMaze *m : done) {
+            cudaStream_t ss = b->side[j++ % mpn_batch::kSide];
             char *res = (char *)arena_at(b, m->res_off);
             GridDev g;
             g.free_bits = (const uint32_t *)arena_at(b, m->planes_off);
@@ -729,14 +762,15 @@ static mpn_status finish_round(mpn_batch *b) {
             g.H = m->H;
             g.W = m->W;
             g.P = m->P;
-            B_TRY(cudaMemsetAsync(res + m->off_o, 0, 8, st));
+            B_TRY(cudaMemsetAsync(res + m->off_o, 0, 8, ss));
             if (m->ns > 0) {
                 B_TRY(launch_trace_lengths(g, m->dist_bits, (const uint32_t *)(res + m->st_o), m->ns,
                                            (uint64_t *)(res + m->off_o), (int8_t *)(res + m->sts_o),
-                                           ctl, st));
-                B_TRY(launch_scan((uint64_t *)(res + m->off_o), m->ns, st));
+                                           ctl, ss));
+                B_TRY(launch_scan((uint64_t *)(res + m->off_o), m->ns, ss));
             }
         }
+        B_TRY(join_side(b));
         std::vector<uint64_t> totals(done.size());
         for (size_t i = 0; i < done.size(); ++i) {
             char *res = (char *)arena_at(b, done[i]->res_off);
@@ -754,16 +788,21 @@ static mpn_status finish_round(mpn_batch *b) {
     // paths of every finished grid whose paths fit in the arena now; the
     // others are traced on demand into the caller's buffer
     bool launched = false;
+    if (!done.empty()) B_TRY(fork_side(b));
+    int j = 0;
     for (HostMaze *m : done) {
         m->cells_bytes = align_up((size_t)(m->total ? m->total : 1) * 4);
         if (!b->mem.alloc(m->cells_bytes, &m->cells_off)) {
             m->cells_bytes = 0;
             continue;
         }
-        if (m->ns > 0) B_TRY(launch_batch_trace(b, *m, (uint32_t *)arena_at(b, m->cells_off)));
+        if (m->ns > 0)
+            B_TRY(launch_batch_trace(b, *m, (uint32_t *)arena_at(b, m->cells_off),
+                                     b->side[j++ % mpn_batch::kSide]));
         m->paths_ready = true;
         launched = true;
     }
+    if (!done.empty()) B_TRY(join_side(b));
     if (launched) B_TRY(cudaStreamSynchronize(st));
     return MPN_OK;
 }
@@ -909,12 +948,12 @@ mpn_status mpn_batch_result(mpn_batch *b, uint64_t ticket, void *dist, uint64_t 
         if (m.paths_ready) {
             B_TRY(cudaMemcpyAsync(cells, arena_at(b, m.cells_off), (size_t)m.total * 4, kind(cells), st));
         } else if (dev_ptr(cells)) {
-            B_TRY(launch_batch_trace(b, m, cells));            // straight into the caller's buffer
+            B_TRY(launch_batch_trace(b, m, cells, st));            // straight into the caller's buffer
         } else {
             // host buffer and no room in the arena: a temporary device buffer
             void *tmp = nullptr;
             B_TRY(cudaMalloc(&tmp, (size_t)m.total * 4));
-            cudaError_t e = launch_batch_trace(b, m, (uint32_t *)tmp);
+            cudaError_t e = launch_batch_trace(b, m, (uint32_t *)tmp, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(cells, tmp, (size_t)m.total * 4, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             cudaFree(tmp);
@@ -991,6 +1030,14 @@ void mpn_batch_destroy(mpn_batch *b) {
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
+    for (int i = 0; i < mpn_batch::kSide; ++i) {
+        if (b->side[i]) {
+            cudaStreamSynchronize(b->side[i]);
+            cudaStreamDestroy(b->side[i]);
+        }
+        if (b->side_ev[i]) cudaEventDestroy(b->side_ev[i]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     delete b;
 }
 

@@ -63,26 +63,24 @@ __device__ __forceinline__ bool grid_barrier(Ctl *c, unsigned target, unsigned s
                                              unsigned *s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned ok = 1;
-        __threadfence();
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u) + 1u;
-        if (arrived < target) {
-            unsigned spins = 0;
-            while (ld_acquire(&c->bar_count) < target) {
-                ++spins;
-                if ((spins & 63u) == 0u && (ld_acquire(&c->err) & ERR_TIMEOUT)) {   // another block gave up
-                    ok = 0;
-                    break;
-                }
-                if (spins > spin_limit) {
-                    atomicOr(&c->err, ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 8) __nanosleep(32);
+        // arrive with release semantics (the block's writes, ordered before
+        // this thread by the block barrier, become visible with it) and wait
+        // with acquire loads: no separate fences
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&c->bar_count) : "memory");
+        unsigned ok = 1, spins = 0;
+        while (ld_acquire(&c->bar_count) < target) {
+            ++spins;
+            if ((spins & 63u) == 0u && (ld_acquire(&c->err) & ERR_TIMEOUT)) {   // another block gave up
+                ok = 0;
+                break;
             }
+            if (spins > spin_limit) {
+                atomicOr(&c->err, ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            if (spins > 8) __nanosleep(32);
         }
-        __threadfence();
         *s_ok = ok;
     }
     __syncthreads();

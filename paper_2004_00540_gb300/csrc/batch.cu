@@ -142,11 +142,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
     __shared__ wave::VisitSmem<RXW, NW> sm;
     __shared__ int s_tile;
     __shared__ unsigned s_mask[2], s_lastj[2], s_done, s_ok;
+    __shared__ uint32_t s_len;   // length of this sweep's list
     Ctl *ctl = &p.bc->c;
     unsigned vq = 0u;
     unsigned long long blk_visits = 0;
     const uint32_t s0 = ld_acquire(&p.bc->next_sweep);
+    const uint32_t G = gridDim.x;
     sm.zero_pad();   // (the first barrier below publishes it)
+    if (threadIdx.x == 0) {
+        // the round's first sweep; later sweeps read their list length and
+        // first entry right after the grid barrier, with the end-of-round test
+        s_len = ld_acquire(&ctl->list_len[s0 % 3]);
+        s_tile = (blockIdx.x < s_len) ? (int)ld_relaxed(p.lists + (size_t)(s0 % 3) * p.max_tiles + blockIdx.x) : -1;
+    }
+    __syncthreads();
 
     for (uint32_t s = s0;; ++s) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -155,10 +164,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
         }
         const uint32_t *list = p.lists + (size_t)(s % 3) * p.max_tiles;
         unsigned *work = &ctl->work[s % 3];
-        const uint32_t len = ld_acquire(&ctl->list_len[s % 3]);
-        const uint32_t G = gridDim.x;
-        if (threadIdx.x == 0) s_tile = (blockIdx.x < len) ? (int)ld_relaxed(list + blockIdx.x) : -1;
-        __syncthreads();
+        const uint32_t len = s_len;
         int t = s_tile;
         const uint32_t stamp = s + 2u;            // queued for sweep s + 1
         const uint32_t sl1 = (s + 1u) % 3u;
@@ -230,14 +236,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
 
         if (!wave::grid_barrier(ctl, (s + 1 - s0) * gridDim.x, p.spin_limit, &s_ok)) return;
         if (threadIdx.x == 0) {
-            const unsigned done = (ld_acquire(&ctl->list_len[(s + 1) % 3]) == 0u) ||
-                                  (p.round_sweeps && s + 1 - s0 >= p.round_sweeps);
+            // one read gives the end-of-round test, the next sweep's list
+            // length and (alongside) this block's first entry of it
+            const uint32_t nlen = ld_acquire(&ctl->list_len[(s + 1) % 3]);
+            const uint32_t *nlist = p.lists + (size_t)((s + 1) % 3) * p.max_tiles;
+            const int first = (blockIdx.x < p.max_tiles) ? (int)ld_relaxed(nlist + blockIdx.x) : -1;
+            const unsigned done = (nlen == 0u) || (p.round_sweeps && s + 1 - s0 >= p.round_sweeps);
             if (done && blockIdx.x == 0) {
                 p.bc->next_sweep = s + 1;
                 ctl->sweeps = s + 1 - s0;
             }
             if (done && blk_visits) atomicAdd(&ctl->visits, blk_visits);
             s_done = done;
+            s_len = nlen;
+            s_tile = (blockIdx.x < nlen) ? first : -1;
         }
         __syncthreads();
         if (s_done) return;

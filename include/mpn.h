@@ -126,6 +126,20 @@ mpn_status mpn_propagate_plain(mpn_ctx *ctx, const uint32_t *targets, int32_t n_
 mpn_status mpn_get_distances(mpn_ctx *ctx, void *dst, int32_t dst_on_device);
 
 /*
+ * Enqueue the same copy (dst: host or device, H*W elements of the context's
+ * dtype) on `stream` (a cudaStream_t; NULL: the context's stream), ordered
+ * after the context's work so far, and return without waiting for it. The
+ * last propagate's errors are reported first (which waits for that propagate
+ * if no call has collected them yet). dst must not be read or freed until the
+ * stream has passed the copy: synchronize that stream, or call mpn_sync on
+ * this context. A later propagate on this context waits, on the device, for
+ * the copy before it rewrites the plane. MPN_ESTATE before the first
+ * propagate. The paper has no counterpart: it lets a caller download one
+ * solve's distances while the next solve's mask goes up and its kernels run.
+ */
+mpn_status mpn_get_distances_async(mpn_ctx *ctx, void *dst, void *stream);
+
+/*
  * The paper's final activity map O after L layers (Methods, "Activity Map
  * Generation"): O = L + 1 - d where d <= L, 0 elsewhere (obstacles,
  * unreached, farther than L). dst: H*W int32, device or host
@@ -186,7 +200,8 @@ mpn_status mpn_trace_euclid(mpn_ctx *ctx, const uint32_t *starts, int32_t n, uin
 mpn_status mpn_nearest_targets(mpn_ctx *ctx, const uint32_t *starts, int32_t n,
                                uint32_t *target, uint32_t *dist);
 
-/* Wait for the context's stream; report any error the GPU recorded. */
+/* Wait for the context's stream and for its pending asynchronous distance
+ * copy (mpn_get_distances_async); report any error the GPU recorded. */
 mpn_status mpn_sync(mpn_ctx *ctx);
 
 void mpn_destroy(mpn_ctx *ctx);

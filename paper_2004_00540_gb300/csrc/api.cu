@@ -151,9 +151,17 @@ struct mpn_ctx {
     bool stats_pending = false;
     Ctl last_ctl{};
 
+    // page-locked, device-mapped host words that small results (the control
+    // block, a path total, an error word) are stored to by k_store_host
+    unsigned char *mbox = nullptr, *mbox_d = nullptr;
+
     cudaEvent_t ev[6] = {};   // encode begin/end, propagate begin/end, trace begin/end
     float ms_encode = 0.f, ms_propagate = 0.f, ms_trace = 0.f;
     bool ev_enc = false, ev_prop = false, ev_trace = false;
+    // asynchronous distance copy: ev_ready orders it after the context's
+    // stream, ev_out marks its end on the copy's stream
+    cudaEvent_t ev_ready = nullptr, ev_out = nullptr;
+    bool out_pending = false;
 
     GridDev grid() const {
         GridDev g;
@@ -169,7 +177,76 @@ struct mpn_ctx {
     size_t dist_bytes() const { return (size_t)H * W * (dist_bits / 8); }
 };
 
+namespace mpn {
+
+// Device-to-host copy by SM stores over the coherent CPU-GPU link rather than
+// a copy engine. Device-to-host copy-engine transfers run in the order they
+// were issued, across streams, so a small read-back on one context's stream
+// would otherwise wait for a large distance download that another context
+// started first; stores from a kernel do not queue behind it.
+__global__ void k_store_host(const unsigned char *__restrict__ src, unsigned char *__restrict__ dst,
+                             size_t bytes) {
+    const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t nt = (size_t)gridDim.x * blockDim.x;
+    const uintptr_t a = (uintptr_t)src | (uintptr_t)dst;
+    size_t done = 0;
+    if ((a & 15) == 0) {
+        const size_t nv = bytes / 16;
+        for (size_t i = t0; i < nv; i += nt) ((uint4 *)dst)[i] = ((const uint4 *)src)[i];
+        done = nv * 16;
+    } else if ((a & 3) == 0) {
+        const size_t nv = bytes / 4;
+        for (size_t i = t0; i < nv; i += nt) ((uint32_t *)dst)[i] = ((const uint32_t *)src)[i];
+        done = nv * 4;
+    }
+    for (size_t i = done + t0; i < bytes; i += nt) dst[i] = src[i];
+}
+
+}  // namespace mpn
+
 namespace {
+
+// Mailbox layout (bytes): the control block, then a path total and an error word.
+constexpr size_t kMboxCtl = 0, kMboxTotal = 128, kMboxErr = 136, kMboxBytes = 256;
+static_assert(sizeof(Ctl) <= kMboxTotal, "control block must fit the mailbox");
+
+cudaError_t store_host(mpn_ctx *c, void *dst_dev, const void *src, size_t bytes) {
+    if (!bytes) return cudaSuccess;
+    const size_t per_block = 256 * 16 * 4;
+    const size_t want = (bytes + per_block - 1) / per_block;
+    const int blocks = (int)(want < (size_t)c->sm_count ? (want ? want : 1) : (size_t)c->sm_count);
+    k_store_host<<<blocks, 256, 0, c->stream>>>((const unsigned char *)src, (unsigned char *)dst_dev,
+                                                bytes);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// The device address of page-locked host memory, else null (device memory,
+// or pageable host memory).
+void *pinned_devptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Copy a device result to the caller's buffer, ordered on the context's
+// stream: device memory by a device-to-device copy, page-locked host memory by
+// k_store_host, pageable host memory by a copy engine.
+cudaError_t copy_out(mpn_ctx *c, void *dst, const void *src, size_t bytes) {
+    if (!bytes) return cudaSuccess;
+    if (is_device_ptr(dst)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (void *d = pinned_devptr(dst)) return store_host(c, d, src, bytes);
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+}
+
+// Store device bytes into the context's mailbox at offset off (read on the
+// host after the stream is synchronized).
+cudaError_t to_mbox(mpn_ctx *c, size_t off, const void *src, size_t bytes) {
+    return store_host(c, c->mbox_d + off, src, bytes);
+}
 
 // Tile geometry and grid size for (variant, depth); allocates the tile queue
 // (a stamp per tile and three tile lists).
@@ -218,6 +295,8 @@ mpn_status alloc_planes(mpn_ctx *c) {
     MPN_TRY(c->dist.ensure(c->dist_bytes()));
     MPN_TRY(c->ctl.ensure(sizeof(Ctl)));
     for (auto &e : c->ev) MPN_TRY(cudaEventCreate(&e));
+    MPN_TRY(cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming));
+    MPN_TRY(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     return auto_configure(c);
 }
 
@@ -236,7 +315,10 @@ mpn_status new_ctx(int32_t H, int32_t W, int32_t dist_bits, void *stream, mpn_ct
     c->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->mbox, kMboxBytes, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&c->mbox_d, c->mbox, 0);
     if (e != cudaSuccess) {
+        if (c->mbox) cudaFreeHost(c->mbox);
         delete c;
         return from_cuda(e);
     }
@@ -289,9 +371,9 @@ mpn_status encode_mask(mpn_ctx *c, const uint8_t *mask) {
 // Collect the device-side result of the last propagate (waits).
 mpn_status finish_propagate(mpn_ctx *c) {
     if (!c->stats_pending) return MPN_OK;
-    MPN_TRY(cudaMemcpyAsync(&c->last_ctl, c->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost,
-                            c->stream));
+    MPN_TRY(to_mbox(c, kMboxCtl, c->ctl.p, sizeof(Ctl)));
     MPN_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(&c->last_ctl, c->mbox + kMboxCtl, sizeof(Ctl));
     c->stats_pending = false;
     c->last_layers = c->last_ctl.max_layer;
     if (c->last_ctl.err) {
@@ -307,6 +389,10 @@ mpn_status begin_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n,
     if (!targets || n < 1) return MPN_EINVAL;
     mpn_status st = finish_propagate(c);   // drain an earlier run's error report
     (void)st;
+    if (c->out_pending) {   // the plane is rewritten below: after the pending copy
+        MPN_TRY(cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+        c->out_pending = false;
+    }
     c->propagated = false;
     if (!is_device_ptr(targets)) {
         const uint64_t N = (uint64_t)c->H * c->W;
@@ -489,8 +575,9 @@ mpn_status mpn_propagate_plain(mpn_ctx *c, const uint32_t *targets, int32_t n,
             MPN_TRY(launch_plain_layer(g, c->dist_bits, layer, ctl, c->stream));
         }
         Ctl h;
-        MPN_TRY(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+        MPN_TRY(to_mbox(c, kMboxCtl, ctl, sizeof(Ctl)));
         MPN_TRY(cudaStreamSynchronize(c->stream));
+        memcpy(&h, c->mbox + kMboxCtl, sizeof(Ctl));
         if (h.err) {
             c->propagated = false;
             return from_err_bits(h.err);
@@ -514,6 +601,7 @@ mpn_status mpn_sync(mpn_ctx *c) {
     if (!c) return MPN_EINVAL;
     mpn_status st = finish_propagate(c);
     if (st != MPN_OK) return st;
+    if (c->out_pending) MPN_TRY(cudaEventSynchronize(c->ev_out));
     return from_cuda(cudaStreamSynchronize(c->stream));
 }
 
@@ -526,6 +614,22 @@ mpn_status mpn_get_distances(mpn_ctx *c, void *dst, int32_t on_device) {
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             c->stream));
     return from_cuda(cudaStreamSynchronize(c->stream));
+}
+
+mpn_status mpn_get_distances_async(mpn_ctx *c, void *dst, void *stream) {
+    if (!c || !dst) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);
+    if (st != MPN_OK) return st;
+    if (!c->propagated) return MPN_ESTATE;
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    if (s != c->stream) {
+        MPN_TRY(cudaEventRecord(c->ev_ready, c->stream));
+        MPN_TRY(cudaStreamWaitEvent(s, c->ev_ready, 0));
+    }
+    MPN_TRY(cudaMemcpyAsync(dst, c->dist.p, c->dist_bytes(), cudaMemcpyDefault, s));
+    MPN_TRY(cudaEventRecord(c->ev_out, s));
+    c->out_pending = true;
+    return MPN_OK;
 }
 
 mpn_status mpn_get_activity(mpn_ctx *c, uint32_t L, int32_t *dst, int32_t on_device) {
@@ -573,10 +677,11 @@ static mpn_status trace_prepare(mpn_ctx *c, const uint32_t *starts, int32_t n,
         MPN_TRY(launch_scan((uint64_t *)c->offsets.p, n, c->stream));
     }
     uint32_t err = 0;
-    MPN_TRY(cudaMemcpyAsync(total, (uint64_t *)c->offsets.p + n, sizeof(uint64_t),
-                            cudaMemcpyDeviceToHost, c->stream));
-    MPN_TRY(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    MPN_TRY(to_mbox(c, kMboxTotal, (uint64_t *)c->offsets.p + n, sizeof(uint64_t)));
+    MPN_TRY(to_mbox(c, kMboxErr, &ctl->err, sizeof(uint32_t)));
     MPN_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(total, c->mbox + kMboxTotal, sizeof(uint64_t));
+    memcpy(&err, c->mbox + kMboxErr, sizeof(uint32_t));
     if (err) return from_err_bits(err);
     return MPN_OK;
 }
@@ -587,9 +692,7 @@ mpn_status mpn_trace_lengths(mpn_ctx *c, const uint32_t *starts, int32_t n, uint
     uint64_t total = 0;
     mpn_status st = trace_prepare(c, starts, n, &ds, &total);
     if (st != MPN_OK) return st;
-    MPN_TRY(cudaMemcpyAsync(offsets, c->offsets.p, (size_t)(n + 1) * sizeof(uint64_t),
-                            is_device_ptr(offsets) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                            c->stream));
+    MPN_TRY(copy_out(c, offsets, c->offsets.p, (size_t)(n + 1) * sizeof(uint64_t)));
     return from_cuda(cudaStreamSynchronize(c->stream));
 }
 
@@ -600,13 +703,8 @@ static mpn_status trace_any(mpn_ctx *c, const uint32_t *starts, int32_t n, uint6
     uint64_t total = 0;
     mpn_status st = trace_prepare(c, starts, n, &ds, &total, euclid);
     if (st != MPN_OK) return st;
-    const bool off_dev = is_device_ptr(offsets), st_dev = n > 0 && is_device_ptr(status);
-    MPN_TRY(cudaMemcpyAsync(offsets, c->offsets.p, (size_t)(n + 1) * sizeof(uint64_t),
-                            off_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
-    if (n > 0)
-        MPN_TRY(cudaMemcpyAsync(status, c->status.p, (size_t)n,
-                                st_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                c->stream));
+    MPN_TRY(copy_out(c, offsets, c->offsets.p, (size_t)(n + 1) * sizeof(uint64_t)));
+    if (n > 0) MPN_TRY(copy_out(c, status, c->status.p, (size_t)n));
     if (total > cells_cap) {
         MPN_TRY(cudaStreamSynchronize(c->stream));
         return MPN_ENOMEM;
@@ -628,12 +726,11 @@ static mpn_status trace_any(mpn_ctx *c, const uint32_t *starts, int32_t n, uint6
                              (const int8_t *)c->status.p, dcells, c->stream, &ctl->err));
     MPN_TRY(cudaEventRecord(c->ev[5], c->stream));
     c->ev_trace = true;
-    if (total > 0 && !cells_dev)
-        MPN_TRY(cudaMemcpyAsync(cells, dcells, (size_t)total * sizeof(uint32_t),
-                                cudaMemcpyDeviceToHost, c->stream));
+    if (total > 0 && !cells_dev) MPN_TRY(copy_out(c, cells, dcells, (size_t)total * sizeof(uint32_t)));
     uint32_t err = 0;
-    MPN_TRY(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    MPN_TRY(to_mbox(c, kMboxErr, &ctl->err, sizeof(uint32_t)));
     MPN_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(&err, c->mbox + kMboxErr, sizeof(uint32_t));
     if (err) return (err & ERR_TRACE) ? MPN_ECUDA : from_err_bits(err);
     return MPN_OK;
 }
@@ -668,11 +765,12 @@ mpn_status mpn_nearest_targets(mpn_ctx *c, const uint32_t *starts, int32_t n, ui
                            c->stream, &ctl->err));
     MPN_TRY(cudaEventRecord(c->ev[5], c->stream));
     c->ev_trace = true;
-    if (!t_dev) MPN_TRY(cudaMemcpyAsync(target, dt, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
-    if (dist && !d_dev) MPN_TRY(cudaMemcpyAsync(dist, dd, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (!t_dev) MPN_TRY(copy_out(c, target, dt, (size_t)n * 4));
+    if (dist && !d_dev) MPN_TRY(copy_out(c, dist, dd, (size_t)n * 4));
     uint32_t err = 0;
-    MPN_TRY(cudaMemcpyAsync(&err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    MPN_TRY(to_mbox(c, kMboxErr, &ctl->err, sizeof(uint32_t)));
     MPN_TRY(cudaStreamSynchronize(c->stream));
+    memcpy(&err, c->mbox + kMboxErr, sizeof(uint32_t));
     if (err) return (err & ERR_TRACE) ? MPN_ECUDA : from_err_bits(err);
     return MPN_OK;
 }
@@ -748,12 +846,16 @@ mpn_status mpn_get_stats(mpn_ctx *c, mpn_stats *out) {
 void mpn_destroy(mpn_ctx *c) {
     if (!c) return;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) cudaGetLastError();
+    if (c->out_pending && cudaEventSynchronize(c->ev_out) != cudaSuccess) cudaGetLastError();
     DevBuf *bufs[] = {&c->free_bits, &c->state, &c->log, &c->log_fill, &c->dist, &c->ctl, &c->tiles,
                       &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
                       &c->cells, &c->activity};
     for (DevBuf *b : bufs) b->release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->mbox) cudaFreeHost(c->mbox);
     delete c;
 }
 

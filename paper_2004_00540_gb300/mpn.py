@@ -25,8 +25,8 @@ MPN_PATH_OK, MPN_PATH_UNREACHABLE, MPN_PATH_ON_OBSTACLE = 0, 1, 2
 # every symbol include/mpn.h declares
 EXPORTS = (
     "mpn_create", "mpn_create_packed", "mpn_set_mask", "mpn_set_stream", "mpn_propagate",
-    "mpn_propagate_plain", "mpn_get_distances", "mpn_get_activity", "mpn_trace_lengths",
-    "mpn_trace", "mpn_sync", "mpn_destroy", "mpn_status_str", "mpn_set_tuning",
+    "mpn_propagate_plain", "mpn_get_distances", "mpn_get_distances_async", "mpn_get_activity",
+    "mpn_trace_lengths", "mpn_trace", "mpn_sync", "mpn_destroy", "mpn_status_str", "mpn_set_tuning",
     "mpn_variant_info", "mpn_get_stats", "mpn_launch_count", "mpn_propagate_noalloc",
     "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_submit", "mpn_batch_run",
     "mpn_batch_poll", "mpn_batch_wait", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
             "mpn_propagate": ([vp, vp, i32, u32, ctypes.POINTER(u32)], ctypes.c_int),
             "mpn_propagate_plain": ([vp, vp, i32, u32, i32, ctypes.POINTER(u32)], ctypes.c_int),
             "mpn_get_distances": ([vp, vp, i32], ctypes.c_int),
+            "mpn_get_distances_async": ([vp, vp, vp], ctypes.c_int),
             "mpn_get_activity": ([vp, u32, vp, i32], ctypes.c_int),
             "mpn_trace_lengths": ([vp, vp, i32, vp], ctypes.c_int),
             "mpn_trace": ([vp, vp, i32, vp, vp, u64, vp], ctypes.c_int),
@@ -223,6 +224,14 @@ def mpn_propagate_plain(ctx, targets, max_layers: int = 0, check_every: int = 1)
 def mpn_get_distances(ctx, out):
     p, dev = _ptr(out)
     _check(load().mpn_get_distances(ctx, p, int(dev)), "mpn_get_distances")
+    return out
+
+
+def mpn_get_distances_async(ctx, out, stream=None):
+    """Enqueue the distance download on `stream` (None: the context's own) and
+    return; `out` is valid once that stream has passed the copy (mpn_sync)."""
+    _check(load().mpn_get_distances_async(ctx, _ptr(out)[0], _stream_handle(stream)),
+           "mpn_get_distances_async")
     return out
 
 

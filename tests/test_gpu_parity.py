@@ -178,6 +178,65 @@ def test_device_tensors_in_and_out():
     assert np.array_equal(status.cpu().numpy(), ostatus)
 
 
+@pytest.mark.parametrize("shift", [0, 1, 4])
+def test_page_locked_host_outputs(shift):
+    """Results read into page-locked host memory (stored by the GPU over the
+    host link), at 16-, 4- and 1-byte alignment, equal the oracle's and those
+    read into pageable memory."""
+    torch = pytest.importorskip("torch")
+    m, t, s = rand_case(613, 900, 0.3, 5, 300, 77)
+    n = s.size
+    with pkg.Planner(m, 32) as pl:
+        pl.propagate(t)
+        off_p = pl.trace(s).offsets              # pageable numpy buffers
+        total = int(off_p[-1])
+        ctx = pl.ctx
+
+        def pinned(nbytes):
+            return torch.zeros(nbytes + 16, dtype=torch.uint8).pin_memory()[shift:shift + nbytes]
+
+        hs = torch.from_numpy(s.astype(np.int32)).pin_memory()
+        off_b, cells_b, st_b = pinned(8 * (n + 1)), pinned(4 * max(total, 1)), pinned(n)
+        assert pkg.mpn_trace(ctx, hs, off_b, cells_b, total, st_b) == pkg.MPN_OK
+        len_b = pinned(8 * (n + 1))
+        pkg.mpn_trace_lengths(ctx, hs, len_b)
+        tgt_b, dist_b = pinned(4 * n), pinned(4 * n)
+        pkg.mpn_nearest_targets(ctx, hs, tgt_b, dist_b)
+        got_t, got_d = pl.nearest_targets(s)
+    d, _ = oracle.bfs(m, t)
+    ooff, ocells, ostatus = oracle.trace(m, d, s)
+    off = off_b.numpy().copy().view(np.uint64)
+    assert np.array_equal(off, ooff) and np.array_equal(off_p, ooff)
+    assert np.array_equal(len_b.numpy().copy().view(np.uint64), ooff)
+    assert np.array_equal(cells_b.numpy().copy().view(np.uint32)[:total], ocells)
+    assert np.array_equal(st_b.numpy().copy().view(np.int8), ostatus)
+    assert np.array_equal(tgt_b.numpy().copy().view(np.uint32), got_t)
+    assert np.array_equal(dist_b.numpy().copy().view(np.uint32), got_d)
+
+
+def test_async_distance_copy_is_ordered_before_the_next_propagate():
+    """mpn_get_distances_async on a side stream, then at once a propagate from
+    other targets on the same context: the copy holds the first plane (the
+    propagate waits for it on the device), and the second plane is right."""
+    torch = pytest.importorskip("torch")
+    m, t, _ = rand_case(1500, 1300, 0.3, 4, 1, 91)
+    t2 = synth.sample_free(m, 2, 92)
+    side = torch.cuda.Stream()
+    h1 = torch.empty((1500, 1300), dtype=torch.int32).pin_memory()
+    h2 = torch.empty((1500, 1300), dtype=torch.int32).pin_memory()
+    with pkg.Planner(m, 32) as pl:
+        pl.propagate(t)
+        pkg.mpn_get_distances_async(pl.ctx, h1, side)
+        pkg.mpn_propagate(pl.ctx, t2.astype(np.uint32), 0, wait=False)
+        pkg.mpn_get_distances_async(pl.ctx, h2)
+        pkg.mpn_sync(pl.ctx)
+        side.synchronize()
+    d1, _ = oracle.bfs(m, t)
+    d2, _ = oracle.bfs(m, t2)
+    assert np.array_equal(h1.numpy().view(np.uint32), d1)
+    assert np.array_equal(h2.numpy().view(np.uint32), d2)
+
+
 @pytest.mark.parametrize("offset", [0, 1, 8])
 def test_device_mask_at_any_alignment(offset):
     """The encoder's vector path needs a 16-byte-aligned mask; a mask at any

@@ -139,7 +139,7 @@ struct mpn_ctx {
     int device = 0, sm_count = 0;
     cudaStream_t stream = nullptr;
 
-    DevBuf free_bits, state, dist, ctl, tiles, mask_stage, log, log_fill;
+    DevBuf free_bits, state, dist, ctl, tiles, mask_stage, log;
     DevBuf targets, starts, offsets, status, cells, activity;
 
     int variant = 0, depth = 32;
@@ -249,7 +249,8 @@ cudaError_t to_mbox(mpn_ctx *c, size_t off, const void *src, size_t bytes) {
 }
 
 // Tile geometry and grid size for (variant, depth); allocates the tile queue
-// (a stamp per tile and three tile lists).
+// (per tile a stamp, the latest log header and the logged-visit count, three
+// tile lists, then the per-tile header slots).
 mpn_status configure(mpn_ctx *c, int variant, int depth) {
     if (variant < 0 || variant >= num_variants()) return MPN_EINVAL;
     const VariantDesc vd = variant_desc(variant);
@@ -268,7 +269,7 @@ mpn_status configure(mpn_ctx *c, int variant, int depth) {
     long long blocks = (long long)bps * c->sm_count;
     if (blocks > ntiles) blocks = ntiles;
     if (blocks < 1) blocks = 1;
-    MPN_TRY(c->tiles.ensure((size_t)ntiles * 4 * sizeof(uint32_t)));
+    MPN_TRY(c->tiles.ensure(((size_t)ntiles * (6 + 4 * kTileSlots) + 4) * sizeof(uint32_t)));
     c->variant = variant;
     c->depth = depth;
     c->TY = TY;
@@ -383,8 +384,11 @@ mpn_status finish_propagate(mpn_ctx *c) {
     return MPN_OK;
 }
 
+// fill_dist: set the distance plane to "unreached" first (the per-layer
+// kernel and a propagation without the activation log write only the cells
+// they reach; the log decode writes every cell).
 mpn_status begin_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n,
-                           const uint32_t **dt) {
+                           const uint32_t **dt, bool fill_dist) {
     if (!c) return MPN_EINVAL;
     if (!targets || n < 1) return MPN_EINVAL;
     mpn_status st = finish_propagate(c);   // drain an earlier run's error report
@@ -401,7 +405,7 @@ mpn_status begin_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n,
     }
     st = stage_u32(c, c->targets, targets, n, dt);
     if (st != MPN_OK) return st;
-    MPN_TRY(cudaMemsetAsync(c->dist.p, 0xff, c->dist_bytes(), c->stream));
+    if (fill_dist) MPN_TRY(cudaMemsetAsync(c->dist.p, 0xff, c->dist_bytes(), c->stream));
     MPN_TRY(cudaMemsetAsync(c->state.p, 0, c->plane_words() * 16, c->stream));
     MPN_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Ctl), c->stream));
     return MPN_OK;
@@ -505,29 +509,33 @@ mpn_status mpn_variant_info(int32_t v, int32_t *rows, int32_t *words, int32_t *t
 
 mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_t max_layers,
                          uint32_t *layers_run) {
-    const uint32_t *dt = nullptr;
-    mpn_status st = begin_propagate(c, targets, n, &dt);
-    if (st != MPN_OK) return st;
-    const size_t ntiles = (size_t)c->ntx * c->nty;
-    MPN_TRY(cudaMemsetAsync(c->tiles.p, 0, ntiles * sizeof(uint32_t), c->stream));
+    if (!c || !targets || n < 1) return MPN_EINVAL;
     // activation log: room for 1.5 entries per plane word plus one partly
     // filled chunk per block (a block that finds it full writes distances
-    // itself, so the size only affects speed)
+    // itself, so the size only affects speed). The TMA-staged variant writes
+    // its distances itself.
     const uint64_t log_entries = c->plane_words() * 3 / 2 + (uint64_t)c->blocks * kLogChunk;
-    uint32_t log_chunks = (uint32_t)((log_entries + kLogChunk - 1) / kLogChunk);
-    if (c->log.ensure((size_t)log_chunks * kLogFields * kLogChunk * sizeof(uint32_t)) != cudaSuccess ||
-        c->log_fill.ensure((size_t)log_chunks * sizeof(uint32_t)) != cudaSuccess) {
+    uint32_t log_chunks = variant_desc(c->variant).tma
+                              ? 0u : (uint32_t)((log_entries + kLogChunk - 1) / kLogChunk);
+    if (log_chunks &&
+        c->log.ensure((size_t)log_chunks * kLogFields * kLogChunk * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();   // no room for the log: the kernel writes distances itself
         c->log.release();
-        c->log_fill.release();
         log_chunks = 0;
     }
-    if (log_chunks)
-        MPN_TRY(cudaMemsetAsync(c->log_fill.p, 0, (size_t)log_chunks * sizeof(uint32_t), c->stream));
+    const uint32_t *dt = nullptr;
+    mpn_status st = begin_propagate(c, targets, n, &dt, log_chunks == 0);
+    if (st != MPN_OK) return st;
+    const size_t ntiles = (size_t)c->ntx * c->nty;
+    // queue stamps, latest log headers and logged-visit counts of every tile
+    MPN_TRY(cudaMemsetAsync(c->tiles.p, 0, 3 * ntiles * sizeof(uint32_t), c->stream));
     PropParams p{};
     p.g = c->grid();
     p.queued = (uint32_t *)c->tiles.p;
-    p.lists = p.queued + ntiles;
+    p.tile_head = p.queued + ntiles;
+    p.tile_nv = p.queued + 2 * ntiles;
+    p.lists = p.queued + 3 * ntiles;
+    p.tile_vis = reinterpret_cast<uint4 *>(p.queued + ((6 * ntiles + 3) & ~(size_t)3));   // 16-byte aligned
     p.ctl = (Ctl *)c->ctl.p;
     p.ntx = c->ntx;
     p.nty = c->nty;
@@ -537,14 +545,13 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     p.max_layers = max_layers;
     p.spin_limit = kSpinLimit;
     p.log = log_chunks ? (uint32_t *)c->log.p : nullptr;
-    p.log_fill = (uint32_t *)c->log_fill.p;
     p.log_chunks = log_chunks;
     const uint64_t bound = (max_layers ? (uint64_t)max_layers : (uint64_t)c->H * c->W) / c->depth + 3;
     p.sweep_cap = (uint32_t)(bound < (1u << 22) ? bound : (1u << 22));
     MPN_TRY(launch_seed(dt, n, p, c->dist_bits, c->stream));
     MPN_TRY(cudaEventRecord(c->ev[2], c->stream));   // times the persistent kernel + log decode
     MPN_TRY(launch_propagate(c->variant, c->dist_bits, p, c->blocks, c->stream));
-    MPN_TRY(launch_log_decode(p, c->dist_bits, c->stream));
+    MPN_TRY(launch_log_decode(p, c->dist_bits, c->sm_count, c->stream));
     MPN_TRY(cudaEventRecord(c->ev[3], c->stream));
     c->ev_prop = true;
     c->stats_pending = true;
@@ -562,7 +569,7 @@ mpn_status mpn_propagate_plain(mpn_ctx *c, const uint32_t *targets, int32_t n,
                                uint32_t max_layers, int32_t check_every, uint32_t *layers_run) {
     if (check_every < 1) return MPN_EINVAL;
     const uint32_t *dt = nullptr;
-    mpn_status st = begin_propagate(c, targets, n, &dt);
+    mpn_status st = begin_propagate(c, targets, n, &dt, true);
     if (st != MPN_OK) return st;
     Ctl *ctl = (Ctl *)c->ctl.p;
     const GridDev g = c->grid();
@@ -847,7 +854,7 @@ void mpn_destroy(mpn_ctx *c) {
     if (!c) return;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) cudaGetLastError();
     if (c->out_pending && cudaEventSynchronize(c->ev_out) != cudaSuccess) cudaGetLastError();
-    DevBuf *bufs[] = {&c->free_bits, &c->state, &c->log, &c->log_fill, &c->dist, &c->ctl, &c->tiles,
+    DevBuf *bufs[] = {&c->free_bits, &c->state, &c->log, &c->dist, &c->ctl, &c->tiles,
                       &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
                       &c->cells, &c->activity};
     for (DevBuf *b : bufs) b->release();

@@ -57,6 +57,9 @@ struct GridDev {
 struct PropParams {
     GridDev g;
     uint32_t *queued;            // per tile: 1 + last sweep it was queued for
+    uint32_t *tile_head;         // per tile: 1 + log index of its latest visit header, 0 = none
+    uint32_t *tile_nv;           // per tile: visits that logged entries
+    uint4 *tile_vis;             // per tile: kTileSlots slots {header index, entry count, l0 + 1, 0} of visit n
     uint32_t *lists;             // 3 tile lists of ntx * nty entries, by sweep mod 3
     Ctl *ctl;
     int ntx, nty;                // tiles
@@ -67,20 +70,29 @@ struct PropParams {
     uint32_t spin_limit;         // barrier wait limit (iterations of ~100 ns)
     uint32_t sweep_cap;          // more sweeps than this is an error
     uint32_t *log;               // activation log (log_chunks chunks), or null
-    uint32_t *log_fill;          // entries written per chunk
     uint32_t log_chunks;
 };
 
 // Activation log: instead of writing distances during a tile visit, the visit
 // records, for every word of its interior in which it reached cells, one
-// entry of kLogFields words -- the word's first cell index (y * W + 32 * word
-// column), the layer of offset 0 (l0 + 1), the reached bits and the five
-// Gray-code counter planes -- and k_log_decode turns the entries into
-// distances after the propagation. A chunk holds kLogChunk entries as
-// kLogFields arrays of kLogChunk words (so a warp's entries are written with
-// coalesced stores); each block fills chunks it takes from a shared pool, and
-// a block that finds the pool empty writes its distances directly.
+// 32-byte entry of kLogFields words -- the word's place in the tile interior
+// (row * TXW + word), the reached bits and the five Gray-code counter planes
+// -- behind a header entry of the visit {1 + index of the tile's previous
+// header (0 = none), entry count, layer of offset 0 (l0 + 1), the visit's
+// number n among the tile's logged visits}. The header becomes the tile's
+// latest (PropParams::tile_head, a chain through the headers), and for n <
+// kTileSlots its index, count and layer also go to the tile's slot n. After
+// the propagation k_log_decode gathers each tile's visits (the slots in
+// parallel, later visits along the chain)
+// and writes every cell of the tile's interior once, so the distance plane
+// needs no fill beforehand. Entries are
+// numbered globally; chunk c holds entries [c * kLogChunk, (c + 1) *
+// kLogChunk), and a visit's header and entries lie in one chunk. Each block
+// fills chunks it takes from a shared pool; a block that finds the pool
+// empty writes its distances directly (and the decode keeps the cells it
+// cannot account for: reached, with no entry).
 constexpr uint32_t kLogChunk = 4096;
+constexpr uint32_t kTileSlots = 64;
 constexpr uint32_t kLogFields = 8;
 
 struct VariantDesc {
@@ -112,7 +124,9 @@ int variant_threads(int v);   // threads per block of variant v
 cudaError_t propagate_blocks_per_sm(int v, int dist_bits, int *out);
 cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int blocks,
                              cudaStream_t st);
-cudaError_t launch_log_decode(const PropParams &p, int dist_bits, cudaStream_t st);
+// k_log_decode over the whole plane (after k_propagate with a log); no-op
+// without one
+cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, cudaStream_t st);
 cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int dist_bits,
                         cudaStream_t st);
 cudaError_t launch_plain_layer(const GridDev &g, int dist_bits, uint32_t layer, Ctl *ctl,

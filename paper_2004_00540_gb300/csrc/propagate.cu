@@ -90,7 +90,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     unsigned long long blk_layers = 0;   // thread 0: layers those visits ran
     unsigned vq = 0u;                    // visit parity (block-uniform)
     bool log_more = p.log != nullptr;    // thread 0: the pool may still have chunks
-    const uint32_t maxv = (uint32_t)(p.TY * p.TXW);   // log entries one visit can need
+    const uint32_t maxv = (uint32_t)(p.TY * p.TXW) + 1u;   // log entries one visit can need
+    unsigned hdr = 0u;                   // thread 0: this visit's header slot in the chunk
+    uint32_t prev_head = 0u;             // thread 0: the tile's latest header before it
+    uint32_t prev_nv = 0u;               // thread 0: the tile's logged visits before it
+    unsigned long long blk_entries = 0;  // thread 0: word entries this block logged
     const wave::LogSink lg{p.log, &s_chunk, &s_cursor};
 
     sm.zero_pad();   // (the first barrier below publishes it)
@@ -150,14 +154,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                 s_mask[vq] = 0u;   // last read two visits ago, before the previous visit's first barrier
                 if (log_more && (s_chunk < 0 || s_cursor + maxv > kLogChunk)) {
                     // this chunk may not hold the visit's entries: take the next one
-                    if (s_chunk >= 0) {
-                        p.log_fill[s_chunk] = s_cursor;
-                        atomicAdd(&ctl->log_entries, (unsigned long long)s_cursor);
-                    }
                     const uint32_t c = atomicAdd(&ctl->log_next, 1u);
                     log_more = c < p.log_chunks;
                     s_chunk = log_more ? (int)c : -1;
                     s_cursor = 0u;
+                }
+                if (s_chunk >= 0) {   // the header goes in front of the visit's entries
+                    hdr = s_cursor;
+                    s_cursor = hdr + 1u;
+                    prev_head = ld_relaxed(p.tile_head + t);   // written before a grid barrier
+                    prev_nv = ld_relaxed(p.tile_nv + t);
                 }
             }
             v.ty = t / p.ntx;
@@ -176,6 +182,23 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                 s_tile = (next_i < len) ? (int)ld_relaxed(list + next_i) : -1;
             }
             __syncthreads();
+            if (threadIdx.x == 0 && s_chunk >= 0) {
+                // the visit's header, unless it logged nothing (then the slot is reused)
+                const uint32_t cnt = s_cursor - hdr - 1u;
+                if (cnt) {
+                    const uint32_t gh = (uint32_t)s_chunk * kLogChunk + hdr;
+                    uint4 *h = reinterpret_cast<uint4 *>(p.log + (size_t)gh * kLogFields);
+                    h[0] = make_uint4(prev_head, cnt, l0 + 1u, prev_nv);
+                    h[1] = make_uint4(0u, 0u, 0u, 0u);
+                    p.tile_head[t] = gh + 1u;
+                    p.tile_nv[t] = prev_nv + 1u;
+                    if (prev_nv < kTileSlots)
+                        p.tile_vis[(size_t)t * kTileSlots + prev_nv] = make_uint4(gh, cnt, l0 + 1u, 0u);
+                    blk_entries += cnt;
+                } else {
+                    s_cursor = hdr;
+                }
+            }
             if (threadIdx.x < 9) {
                 if (pend_new) p.lists[(size_t)slot1 * ntl + pend_i] = (uint32_t)pend_t;
                 // this visit's push for border zone threadIdx.x: stamp now, append later
@@ -218,73 +241,203 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             if (thr_maxl) atomicMax(&s_maxl, thr_maxl);
             __syncthreads();
             if (threadIdx.x == 0 && s_maxl) atomicMax(&ctl->max_layer, s_maxl);
-            if (threadIdx.x == 0 && s_chunk >= 0) {
-                p.log_fill[s_chunk] = s_cursor;
-                atomicAdd(&ctl->log_entries, (unsigned long long)s_cursor);
-            }
+            if (threadIdx.x == 0 && blk_entries) atomicAdd(&ctl->log_entries, blk_entries);
             return;
         }
     }
 }
 
-// Distances from the activation log, after the propagation: a block takes a
-// chunk, a warp 32 entries of it at a time (one per lane, coalesced field
-// loads); each lane turns its entry's
-// Gray planes into binary planes (four XORs for all 32 cells) and packs the
-// 32 layer offsets as bytes into shared memory (four cells per word: each
-// plane's nibble is spread to one bit per byte with a multiply), then the
-// warp writes the entries' reached cells one entry at a time, 32 consecutive
-// cells per coalesced store. Entries of one word from different visits hold
-// disjoint reached bits, so the order does not matter. An entry whose first
-// cell lies outside the grid is skipped (defensive; the kernel never writes
-// one).
+// Distances from the activation log, after the propagation, tile by tile: a
+// block takes a tile and assembles a band of its interior (all of it for the
+// usual tile shapes) in shared memory, then writes the band's rows with
+// coalesced stores, each cell once. The tile's visits come from its slots
+// (loaded in parallel) and, past kTileSlots visits, from the chain through
+// the headers, up to kDecodeBatch at a time. Each lane takes one entry
+// (32-byte loads, consecutive across the warp), turns its Gray planes into
+// binary planes (four XORs for all 32 cells), packs four cells' offsets as
+// bytes with one multiply per plane nibble, and stores the layers of its
+// reached cells into the word's 33-word row slot (the pad spreads the lanes'
+// words over the banks). Entries of one word from different visits hold
+// disjoint reached bits, so the order does not matter. A cell still empty
+// afterwards is unreached (the unreached value, which for uint32 equals the
+// empty mark) unless the propagation reached it without an entry -- a
+// target, or a cell a block wrote directly once the pool ran out -- whose
+// value is then read back from the plane so that it is written unchanged.
+// Indices outside the pool end the tile's walk (defensive; the propagation
+// never writes one).
+constexpr int kDecodeBatch = 64;
+
 __device__ __forceinline__ uint32_t spread_nibble(uint32_t n) {   // bit i -> bit 8 i
     return (n * 0x204081u) & 0x01010101u;
 }
 
+// shared memory words of a band of `rows` rows: layers (33 per word), then
+// reached and covered bits per word
+__host__ __device__ inline size_t decode_band_words(int rows, int txw) {
+    return (size_t)rows * txw * 35;
+}
+
 template <typename DT>
-__global__ void __launch_bounds__(256) k_log_decode(const uint32_t *log, const uint32_t *fill,
-                                                    const Ctl *ctl, uint32_t chunks, void *dist,
-                                                    uint32_t ncells, uint32_t *err) {
-    __shared__ uint32_t sb[8][32][9];   // per warp: 32 entries x 8 words of 4 byte offsets (+ pad)
+__global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows, uint32_t txw_magic) {
+    extern __shared__ __align__(16) uint32_t buf[];
+    __shared__ uint32_t s_gh[kDecodeBatch], s_cnt[kDecodeBatch], s_lay[kDecodeBatch];
+    __shared__ uint32_t s_start[kDecodeBatch + 1];
+    __shared__ uint32_t s_nvis, s_chain, s_bad;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t used = min(ctl->log_next, chunks);
-    for (uint32_t c = blockIdx.x; c < used; c += gridDim.x) {
-        const uint32_t n = min(fill[c], kLogChunk);
-        const uint32_t *base = log + (size_t)c * (kLogFields * kLogChunk);
-        for (uint32_t g = (uint32_t)warp * 32u; g < n; g += 256u) {
-            const uint32_t e = g + (uint32_t)lane;
-            uint32_t cell0 = 0xffffffffu, nb = 0u, lay = 0u, pl[5] = {0u, 0u, 0u, 0u, 0u};
-            if (e < n) {
-                cell0 = base[e];
-                lay = base[kLogChunk + e];
-                nb = base[2 * kLogChunk + e];
-#pragma unroll
-                for (int b = 0; b < 5; ++b) pl[b] = base[(3 + b) * kLogChunk + e];
+    const GridDev &g = p.g;
+    const int TXW = p.TXW, TY = p.TY, CW = TXW * 32, RW = TXW * 33;   // RW: buffer words per row
+    const uint32_t cap = p.log_chunks * kLogChunk;
+    constexpr uint32_t kNone = 0xffffffffu;
+    uint32_t *sV = buf + (size_t)band_rows * RW;          // reached bits per word
+    uint32_t *sC = sV + (size_t)band_rows * TXW;          // bits covered by entries per word
+    const int ntiles = p.ntx * p.nty;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int ty = t / p.ntx, tx = t - ty * p.ntx;
+        const int ybase = ty * TY, xbase = tx * CW;
+        const int rows = min(TY, g.H - ybase), cols = min(CW, g.W - xbase);
+        const uint32_t nv = p.tile_nv[t];
+        // slot threadIdx.x (read only below nv)
+        const uint4 slot = threadIdx.x < kTileSlots ? p.tile_vis[(size_t)t * kTileSlots + threadIdx.x]
+                                                    : make_uint4(0u, 0u, 0u, 0u);
+        for (int b0 = 0; b0 < rows; b0 += band_rows) {
+            const int br = min(band_rows, rows - b0);
+            {
+                const int n = br * RW;
+                uint4 *b4 = reinterpret_cast<uint4 *>(buf);
+                for (int i = threadIdx.x; i < n / 4; i += 256) b4[i] = make_uint4(kNone, kNone, kNone, kNone);
+                for (int i = (n & ~3) + threadIdx.x; i < n; i += 256) buf[i] = kNone;
             }
-            if (cell0 >= ncells) nb = 0u;
-#pragma unroll
-            for (int b = 3; b >= 0; --b) pl[b] ^= pl[b + 1];   // Gray -> binary, bit-sliced
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                uint32_t off4 = 0u;
-#pragma unroll
-                for (int b = 0; b < 5; ++b) off4 += spread_nibble((pl[b] >> (4 * q)) & 0xfu) << b;
-                sb[warp][lane][q] = off4;
-            }
-            __syncwarp();
-            const uint32_t m = min(32u, n - g);
-            for (uint32_t j = 0; j < m; ++j) {
-                const uint32_t c0 = __shfl_sync(0xffffffffu, cell0, (int)j);
-                const uint32_t bj = __shfl_sync(0xffffffffu, nb, (int)j);
-                const uint32_t lj = __shfl_sync(0xffffffffu, lay, (int)j);
-                if ((bj >> lane) & 1u) {
-                    const uint32_t layer = lj + ((sb[warp][j][lane >> 2] >> (8 * (lane & 3))) & 0xffu);
-                    if (sizeof(DT) == 2 && layer > 0xfffeu) atomicOr(err, ERR_OVERFLOW);
-                    else reinterpret_cast<DT *>(dist)[c0 + (uint32_t)lane] = (DT)layer;
+            for (int r = warp; r < br; r += 8) {
+                const int gw = tx * TXW + lane;
+                if (lane < TXW) {
+                    sV[r * TXW + lane] = gw < g.P ? g.state[4 * ((size_t)(ybase + b0 + r) * g.P + gw)] : 0u;
+                    sC[r * TXW + lane] = 0u;
                 }
             }
-            __syncwarp();
+            uint32_t done = 0;   // visits placed (block-uniform)
+            if (threadIdx.x == 0) {
+                s_chain = p.tile_head[t];
+                s_bad = 0u;
+            }
+            while (done < nv) {
+                // ---- gather a batch of visits: {header index, count, l0 + 1} ----
+                __syncthreads();   // the previous batch's lists are no longer read
+                uint32_t nb_vis;
+                if (done == 0) {   // the slots (the loads went out with nv's)
+                    nb_vis = min(nv, kTileSlots);
+                    if (threadIdx.x < nb_vis) {
+                        const uint32_t gh = slot.x;
+                        s_gh[threadIdx.x] = gh;
+                        s_cnt[threadIdx.x] = gh < cap ? min(slot.y, cap - gh - 1u) : 0u;
+                        s_lay[threadIdx.x] = slot.z;
+                    }
+                } else {
+                    if (threadIdx.x == 0) {
+                        // the chain holds the visits past the slots, newest first
+                        uint32_t n = 0u, h = s_chain;
+                        const uint32_t want = min((uint32_t)kDecodeBatch, nv - done);
+                        while (n < want && h != 0u && h - 1u < cap) {
+                            const uint32_t gh = h - 1u;
+                            const uint4 hd = *reinterpret_cast<const uint4 *>(p.log + (size_t)gh * kLogFields);
+                            if (hd.w < kTileSlots) break;   // the rest sit in slots
+                            s_gh[n] = gh;
+                            s_cnt[n] = min(hd.y, cap - gh - 1u);
+                            s_lay[n] = hd.z;
+                            ++n;
+                            h = hd.x;
+                        }
+                        s_chain = h;
+                        s_bad = n < want;   // a broken chain: stop after this batch
+                        s_nvis = n;
+                    }
+                    __syncthreads();
+                    nb_vis = s_nvis;
+                }
+                __syncthreads();
+                if (warp == 0) {   // exclusive prefix of the counts (kDecodeBatch = 2 x 32)
+                    const uint32_t c0 = lane < (int)nb_vis ? s_cnt[lane] : 0u;
+                    const uint32_t c1 = lane + 32 < (int)nb_vis ? s_cnt[lane + 32] : 0u;
+                    uint32_t i0 = c0, i1 = c1;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t u0 = __shfl_up_sync(0xffffffffu, i0, d);
+                        const uint32_t u1 = __shfl_up_sync(0xffffffffu, i1, d);
+                        if (lane >= d) {
+                            i0 += u0;
+                            i1 += u1;
+                        }
+                    }
+                    const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31);
+                    s_start[lane] = i0 - c0;
+                    s_start[lane + 32] = tot0 + i1 - c1;
+                    if (lane == 31) s_start[64] = tot0 + i1;
+                }
+                __syncthreads();
+                // ---- place the batch's entries, one per thread ----
+                const uint32_t total = s_start[nb_vis];
+                uint32_t vi = 0;   // visit of entry f (f only grows)
+                for (uint32_t f = threadIdx.x; f < total; f += 256u) {
+                    while (s_start[vi + 1] <= f) ++vi;
+                    const uint4 *ep = reinterpret_cast<const uint4 *>(
+                        p.log + (size_t)(s_gh[vi] + 1u + (f - s_start[vi])) * kLogFields);
+                    const uint4 a = ep[0], b = ep[1];   // {pos, NB, P0, P1}, {P2, P3, P4, 0}
+                    // a.x / TXW by multiplication (exact for a.x < 2^16; larger is out of band)
+                    const uint32_t row = a.x < 65536u ? __umulhi(a.x, txw_magic) : 0xffffffffu;
+                    const uint32_t word = a.x - row * (uint32_t)TXW;
+                    if (row - (uint32_t)b0 >= (uint32_t)br) continue;   // another band (or bad)
+                    const uint32_t nb = a.y, lay = s_lay[vi];
+                    uint32_t B[5] = {a.z, a.w, b.x, b.y, b.z};
+#pragma unroll
+                    for (int q = 3; q >= 0; --q) B[q] ^= B[q + 1];   // Gray -> binary, bit-sliced
+                    const uint32_t w = (row - (uint32_t)b0) * (uint32_t)TXW + word;
+                    atomicOr(&sC[w], nb);
+                    uint32_t *dst = buf + (row - (uint32_t)b0) * (uint32_t)RW + word * 33u;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        uint32_t off4 = 0u;
+#pragma unroll
+                        for (int bb = 0; bb < 5; ++bb) off4 += spread_nibble((B[bb] >> (4 * q)) & 0xfu) << bb;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if ((nb >> (4 * q + i)) & 1u) dst[4 * q + i] = lay + ((off4 >> (8 * i)) & 0xffu);
+                    }
+                }
+                done += nb_vis;
+                if (s_bad || nb_vis == 0) break;   // block-uniform
+            }
+            __syncthreads();
+            // ---- reached cells without an entry keep their value ----
+            for (int i = threadIdx.x; i < br * TXW; i += 256) {
+                uint32_t m = sV[i] & ~sC[i];
+                if (!m) continue;
+                const int r = i / TXW, word = i - r * TXW;
+                const DT *src = reinterpret_cast<const DT *>(g.dist) + (size_t)(ybase + b0 + r) * g.W +
+                                xbase + word * 32;
+                while (m) {
+                    const int c = __ffs(m) - 1;
+                    m &= m - 1u;
+                    if (xbase + word * 32 + c < g.W) buf[r * RW + word * 33 + c] = (uint32_t)src[c];
+                }
+            }
+            __syncthreads();
+            // ---- write the band: every cell of it ----
+            for (int r = warp; r < br; r += 8) {
+                DT *d = reinterpret_cast<DT *>(g.dist) + (size_t)(ybase + b0 + r) * g.W + xbase + lane;
+                const uint32_t *src = buf + r * RW + lane;
+#pragma unroll 4
+                for (int w = 0; w < TXW; ++w) {   // word w: cells 32 w + lane
+                    if (32 * w + lane < cols) {
+                        const uint32_t val = src[33 * w];
+                        if (sizeof(DT) == 2) {
+                            if (val != kNone && val > 0xfffeu) atomicOr(&p.ctl->err, ERR_OVERFLOW);
+                            d[32 * w] = (DT)(val > 0xfffeu ? 0xffffu : val);
+                        } else {
+                            d[32 * w] = (DT)val;
+                        }
+                    }
+                }
+            }
+            __syncthreads();   // before the next band or tile refills the buffer
         }
     }
 }
@@ -717,17 +870,38 @@ cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int bloc
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(variant_threads(v)), args, 0, st);
 }
 
-cudaError_t launch_log_decode(const PropParams &p, int dist_bits, cudaStream_t st) {
-    if (!p.log || !p.log_chunks) return cudaSuccess;
-    const uint32_t ncells = (uint32_t)((uint64_t)p.g.H * (uint64_t)p.g.W);
-    const int blocks = (int)(p.log_chunks < 152u * 8u ? p.log_chunks : 152u * 8u);
+cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, cudaStream_t st) {
+    if (!p.log) return cudaSuccess;
+    if (p.TXW < 2 || p.TY * p.TXW >= 65536) return cudaErrorInvalidValue;   // (every tiling has these)
+    // a band of at most 32 KB of layers (half an interior for the usual tile
+    // shapes: six blocks per SM keep more loads in flight than three blocks
+    // with whole interiors), plus its reached and covered words
+    int band = (32 * 1024) / (p.TXW * 33 * 4);
+    band = band < 1 ? 1 : (band > p.TY ? p.TY : band);
+    const size_t smem = decode_band_words(band, p.TXW) * sizeof(uint32_t);
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        // the largest shared-memory carveout, so that six blocks fit per SM
+        const void *fns[2] = {(const void *)k_log_decode<uint16_t>, (const void *)k_log_decode<uint32_t>};
+        for (const void *f : fns) {
+            if (attr == cudaSuccess)
+                attr = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 * 1024);
+            if (attr == cudaSuccess)
+                attr = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            cudaSharedmemCarveoutMaxShared);
+        }
+    });
+    if (attr != cudaSuccess) return attr;
+    const int ntiles = p.ntx * p.nty;
+    const int most = sm_count * 6;
+    const int blocks = ntiles < most ? ntiles : most;
     count_launch();
+    const uint32_t magic = (uint32_t)((0x100000000ull + (uint64_t)p.TXW - 1) / (uint64_t)p.TXW);
     if (dist_bits == 16)
-        k_log_decode<uint16_t><<<blocks, 256, 0, st>>>(p.log, p.log_fill, p.ctl, p.log_chunks,
-                                                        p.g.dist, ncells, &p.ctl->err);
+        k_log_decode<uint16_t><<<blocks, 256, smem, st>>>(p, band, magic);
     else
-        k_log_decode<uint32_t><<<blocks, 256, 0, st>>>(p.log, p.log_fill, p.ctl, p.log_chunks,
-                                                        p.g.dist, ncells, &p.ctl->err);
+        k_log_decode<uint32_t><<<blocks, 256, smem, st>>>(p, band, magic);
     return cudaGetLastError();
 }
 

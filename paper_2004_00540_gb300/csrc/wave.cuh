@@ -177,8 +177,9 @@ __device__ __forceinline__ int xslot(int g, int w) {
 
 // Where a visit leaves its activation records: chunk *s_chunk of the
 // activation log, with *s_cursor entries already used (both in shared memory,
-// set by the block before the visit's first barrier). No log, or
-// *s_chunk < 0: the visit writes its distances itself.
+// set by the block before the visit's first barrier; the block has reserved
+// the visit's header entry in front of them). No log, or *s_chunk < 0: the
+// visit writes its distances itself.
 struct LogSink {
     uint32_t *log = nullptr;
     const int *s_chunk = nullptr;
@@ -391,8 +392,9 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WP
     const int chunk = lg.log ? *lg.s_chunk : -1;   // block-uniform
     if (chunk >= 0) {
         // one activation-log entry per changed word: the warp reserves its
-        // entries with one shared-memory atomic and writes them field by field
-        uint32_t *base = lg.log + (size_t)chunk * (kLogFields * kLogChunk);
+        // entries with one shared-memory atomic and writes each as two 16-byte
+        // stores (the warp's entries are consecutive)
+        const uint32_t cbase = (uint32_t)chunk * kLogChunk;
         unsigned act[S];
         uint32_t tot = 0u;
 #pragma unroll
@@ -407,13 +409,13 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WP
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             if (NB[s]) {
-                uint32_t *e = base + at + (uint32_t)__popc(act[s] & below);
-                e[0 * kLogChunk] = (uint32_t)(y0 + r0 + s / WPL) * (uint32_t)gd.W +
-                                   (uint32_t)(gw0 + s % WPL) * 32u;
-                e[1 * kLogChunk] = v.l0 + 1u;
-                e[2 * kLogChunk] = NB[s];
-#pragma unroll
-                for (int b = 0; b < 5; ++b) e[(3 + b) * kLogChunk] = P[b][s];
+                const uint32_t idx = cbase + at + (uint32_t)__popc(act[s] & below);
+                uint4 *e = reinterpret_cast<uint4 *>(lg.log + (size_t)idx * kLogFields);
+                // the word's place in the tile interior: row * TXW + word
+                const uint32_t pos = (uint32_t)(r0 + s / WPL - k) * (uint32_t)TXW +
+                                     (uint32_t)(wl * WPL + s % WPL - 1);
+                e[0] = make_uint4(pos, NB[s], P[0][s], P[1][s]);
+                e[1] = make_uint4(P[2][s], P[3][s], P[4][s], 0u);
             }
             at += (uint32_t)__popc(act[s]);
         }

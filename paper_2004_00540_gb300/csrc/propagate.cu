@@ -277,15 +277,16 @@ __host__ __device__ inline size_t decode_band_words(int rows, int txw) {
     return (size_t)rows * txw * 35;
 }
 
-template <typename DT>
-__global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows, uint32_t txw_magic) {
+template <typename DT, int TXW>
+__global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows) {
     extern __shared__ __align__(16) uint32_t buf[];
     __shared__ uint32_t s_gh[kDecodeBatch], s_cnt[kDecodeBatch], s_lay[kDecodeBatch];
     __shared__ uint32_t s_start[kDecodeBatch + 1];
     __shared__ uint32_t s_nvis, s_chain, s_bad;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const GridDev &g = p.g;
-    const int TXW = p.TXW, TY = p.TY, CW = TXW * 32, RW = TXW * 33;   // RW: buffer words per row
+    const int TY = p.TY;
+    constexpr int CW = TXW * 32, RW = TXW * 33;   // RW: buffer words per row
     const uint32_t cap = p.log_chunks * kLogChunk;
     constexpr uint32_t kNone = 0xffffffffu;
     uint32_t *sV = buf + (size_t)band_rows * RW;          // reached bits per word
@@ -381,9 +382,7 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
                     const uint4 *ep = reinterpret_cast<const uint4 *>(
                         p.log + (size_t)(s_gh[vi] + 1u + (f - s_start[vi])) * kLogFields);
                     const uint4 a = ep[0], b = ep[1];   // {pos, NB, P0, P1}, {P2, P3, P4, 0}
-                    // a.x / TXW by multiplication (exact for a.x < 2^16; larger is out of band)
-                    const uint32_t row = a.x < 65536u ? __umulhi(a.x, txw_magic) : 0xffffffffu;
-                    const uint32_t word = a.x - row * (uint32_t)TXW;
+                    const uint32_t row = a.x / (uint32_t)TXW, word = a.x - row * (uint32_t)TXW;
                     if (row - (uint32_t)b0 >= (uint32_t)br) continue;   // another band (or bad)
                     const uint32_t nb = a.y, lay = s_lay[vi];
                     uint32_t B[5] = {a.z, a.w, b.x, b.y, b.z};
@@ -424,7 +423,7 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
             for (int r = warp; r < br; r += 8) {
                 DT *d = reinterpret_cast<DT *>(g.dist) + (size_t)(ybase + b0 + r) * g.W + xbase + lane;
                 const uint32_t *src = buf + r * RW + lane;
-#pragma unroll 4
+#pragma unroll
                 for (int w = 0; w < TXW; ++w) {   // word w: cells 32 w + lane
                     if (32 * w + lane < cols) {
                         const uint32_t val = src[33 * w];
@@ -870,20 +869,19 @@ cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int bloc
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(variant_threads(v)), args, 0, st);
 }
 
-cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, cudaStream_t st) {
-    if (!p.log) return cudaSuccess;
-    if (p.TXW < 2 || p.TY * p.TXW >= 65536) return cudaErrorInvalidValue;   // (every tiling has these)
+template <int TXW>
+static cudaError_t launch_decode_txw(const PropParams &p, int dist_bits, int sm_count, cudaStream_t st) {
     // a band of at most 32 KB of layers (half an interior for the usual tile
     // shapes: six blocks per SM keep more loads in flight than three blocks
     // with whole interiors), plus its reached and covered words
-    int band = (32 * 1024) / (p.TXW * 33 * 4);
+    int band = (32 * 1024) / (TXW * 33 * 4);
     band = band < 1 ? 1 : (band > p.TY ? p.TY : band);
-    const size_t smem = decode_band_words(band, p.TXW) * sizeof(uint32_t);
+    const size_t smem = decode_band_words(band, TXW) * sizeof(uint32_t);
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
         // the largest shared-memory carveout, so that six blocks fit per SM
-        const void *fns[2] = {(const void *)k_log_decode<uint16_t>, (const void *)k_log_decode<uint32_t>};
+        const void *fns[2] = {(const void *)k_log_decode<uint16_t, TXW>, (const void *)k_log_decode<uint32_t, TXW>};
         for (const void *f : fns) {
             if (attr == cudaSuccess)
                 attr = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 72 * 1024);
@@ -897,12 +895,21 @@ cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, 
     const int most = sm_count * 6;
     const int blocks = ntiles < most ? ntiles : most;
     count_launch();
-    const uint32_t magic = (uint32_t)((0x100000000ull + (uint64_t)p.TXW - 1) / (uint64_t)p.TXW);
     if (dist_bits == 16)
-        k_log_decode<uint16_t><<<blocks, 256, smem, st>>>(p, band, magic);
+        k_log_decode<uint16_t, TXW><<<blocks, 256, smem, st>>>(p, band);
     else
-        k_log_decode<uint32_t><<<blocks, 256, smem, st>>>(p, band, magic);
+        k_log_decode<uint32_t, TXW><<<blocks, 256, smem, st>>>(p, band);
     return cudaGetLastError();
+}
+
+cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, cudaStream_t st) {
+    if (!p.log) return cudaSuccess;
+    switch (p.TXW) {   // interior words of a tile: region words (4, 8 or 16) - 2
+        case 2: return launch_decode_txw<2>(p, dist_bits, sm_count, st);
+        case 6: return launch_decode_txw<6>(p, dist_bits, sm_count, st);
+        case 14: return launch_decode_txw<14>(p, dist_bits, sm_count, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int dist_bits,

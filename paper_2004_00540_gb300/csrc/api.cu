@@ -3,6 +3,7 @@
 // declared and documented in include/mpn.h.
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -517,6 +518,14 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     const uint64_t log_entries = c->plane_words() * 3 / 2 + (uint64_t)c->blocks * kLogChunk;
     uint32_t log_chunks = variant_desc(c->variant).tma
                               ? 0u : (uint32_t)((log_entries + kLogChunk - 1) / kLogChunk);
+    // test hooks for the fallback paths: a smaller pool (MPN_TEST_LOG_CHUNKS;
+    // 0 = no log), fewer decode slots (MPN_TEST_DECODE_SLOTS)
+    if (const char *e = getenv("MPN_TEST_LOG_CHUNKS")) {
+        const long v = strtol(e, nullptr, 10);
+        if (v >= 0 && (uint64_t)v < log_chunks) log_chunks = (uint32_t)v;
+    }
+    uint32_t slots = kTileSlots;
+    if (const char *e = getenv("MPN_TEST_DECODE_SLOTS")) slots = (uint32_t)strtoul(e, nullptr, 10);
     if (log_chunks &&
         c->log.ensure((size_t)log_chunks * kLogFields * kLogChunk * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();   // no room for the log: the kernel writes distances itself
@@ -551,7 +560,7 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     MPN_TRY(launch_seed(dt, n, p, c->dist_bits, c->stream));
     MPN_TRY(cudaEventRecord(c->ev[2], c->stream));   // times the persistent kernel + log decode
     MPN_TRY(launch_propagate(c->variant, c->dist_bits, p, c->blocks, c->stream));
-    MPN_TRY(launch_log_decode(p, c->dist_bits, c->sm_count, c->stream));
+    MPN_TRY(launch_log_decode(p, c->dist_bits, c->sm_count, slots, c->stream));
     MPN_TRY(cudaEventRecord(c->ev[3], c->stream));
     c->ev_prop = true;
     c->stats_pending = true;

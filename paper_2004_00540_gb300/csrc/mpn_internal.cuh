@@ -125,8 +125,10 @@ cudaError_t propagate_blocks_per_sm(int v, int dist_bits, int *out);
 cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int blocks,
                              cudaStream_t st);
 // k_log_decode over the whole plane (after k_propagate with a log); no-op
-// without one
-cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, cudaStream_t st);
+// without one. slots (1..kTileSlots, else kTileSlots): how many of a tile's
+// visits the decode takes from its slots before the header chain.
+cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, uint32_t slots,
+                              cudaStream_t st);
 cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int dist_bits,
                         cudaStream_t st);
 cudaError_t launch_plain_layer(const GridDev &g, int dist_bits, uint32_t layer, Ctl *ctl,

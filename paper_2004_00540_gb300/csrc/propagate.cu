@@ -278,7 +278,7 @@ __host__ __device__ inline size_t decode_band_words(int rows, int txw) {
 }
 
 template <typename DT, int TXW>
-__global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows) {
+__global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows, uint32_t slots) {
     extern __shared__ __align__(16) uint32_t buf[];
     __shared__ uint32_t s_gh[kDecodeBatch], s_cnt[kDecodeBatch], s_lay[kDecodeBatch];
     __shared__ uint32_t s_start[kDecodeBatch + 1];
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows)
         const int rows = min(TY, g.H - ybase), cols = min(CW, g.W - xbase);
         const uint32_t nv = p.tile_nv[t];
         // slot threadIdx.x (read only below nv)
-        const uint4 slot = threadIdx.x < kTileSlots ? p.tile_vis[(size_t)t * kTileSlots + threadIdx.x]
+        const uint4 slot = threadIdx.x < slots ? p.tile_vis[(size_t)t * kTileSlots + threadIdx.x]
                                                     : make_uint4(0u, 0u, 0u, 0u);
         for (int b0 = 0; b0 < rows; b0 += band_rows) {
             const int br = min(band_rows, rows - b0);
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows)
                 __syncthreads();   // the previous batch's lists are no longer read
                 uint32_t nb_vis;
                 if (done == 0) {   // the slots (the loads went out with nv's)
-                    nb_vis = min(nv, kTileSlots);
+                    nb_vis = min(nv, slots);
                     if (threadIdx.x < nb_vis) {
                         const uint32_t gh = slot.x;
                         s_gh[threadIdx.x] = gh;
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows)
                         while (n < want && h != 0u && h - 1u < cap) {
                             const uint32_t gh = h - 1u;
                             const uint4 hd = *reinterpret_cast<const uint4 *>(p.log + (size_t)gh * kLogFields);
-                            if (hd.w < kTileSlots) break;   // the rest sit in slots
+                            if (hd.w < slots) break;   // the rest sit in slots
                             s_gh[n] = gh;
                             s_cnt[n] = min(hd.y, cap - gh - 1u);
                             s_lay[n] = hd.z;
@@ -870,7 +870,8 @@ cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int bloc
 }
 
 template <int TXW>
-static cudaError_t launch_decode_txw(const PropParams &p, int dist_bits, int sm_count, cudaStream_t st) {
+static cudaError_t launch_decode_txw(const PropParams &p, int dist_bits, int sm_count, uint32_t slots,
+                                     cudaStream_t st) {
     // a band of at most 32 KB of layers (half an interior for the usual tile
     // shapes: six blocks per SM keep more loads in flight than three blocks
     // with whole interiors), plus its reached and covered words
@@ -896,18 +897,20 @@ static cudaError_t launch_decode_txw(const PropParams &p, int dist_bits, int sm_
     const int blocks = ntiles < most ? ntiles : most;
     count_launch();
     if (dist_bits == 16)
-        k_log_decode<uint16_t, TXW><<<blocks, 256, smem, st>>>(p, band);
+        k_log_decode<uint16_t, TXW><<<blocks, 256, smem, st>>>(p, band, slots);
     else
-        k_log_decode<uint32_t, TXW><<<blocks, 256, smem, st>>>(p, band);
+        k_log_decode<uint32_t, TXW><<<blocks, 256, smem, st>>>(p, band, slots);
     return cudaGetLastError();
 }
 
-cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, cudaStream_t st) {
+cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, uint32_t slots,
+                              cudaStream_t st) {
     if (!p.log) return cudaSuccess;
+    if (slots < 1 || slots > kTileSlots) slots = kTileSlots;
     switch (p.TXW) {   // interior words of a tile: region words (4, 8 or 16) - 2
-        case 2: return launch_decode_txw<2>(p, dist_bits, sm_count, st);
-        case 6: return launch_decode_txw<6>(p, dist_bits, sm_count, st);
-        case 14: return launch_decode_txw<14>(p, dist_bits, sm_count, st);
+        case 2: return launch_decode_txw<2>(p, dist_bits, sm_count, slots, st);
+        case 6: return launch_decode_txw<6>(p, dist_bits, sm_count, slots, st);
+        case 14: return launch_decode_txw<14>(p, dist_bits, sm_count, slots, st);
         default: return cudaErrorInvalidValue;
     }
 }

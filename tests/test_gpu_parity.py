@@ -334,6 +334,32 @@ def test_activation_log_counts_match_the_oracle():
     assert st["log_entries"] == pairs.size
 
 
+@pytest.mark.parametrize("chunks,slots", [("0", ""), ("1", ""), ("3", ""), ("", "1"), ("2", "2")])
+def test_log_fallbacks_stay_exact(chunks, slots, monkeypatch):
+    """The activation log's fallback paths, forced through test hooks: no log
+    (the plane is filled and every block writes its distances), a pool of a
+    few chunks (most blocks write directly; the decode keeps their cells), and
+    a decode that takes only the first visits of a tile from its slots and the
+    rest from the header chain. Distances and layer counts equal the oracle's
+    on a maze (many visits per tile) and a Bernoulli grid, both dtypes."""
+    if chunks:
+        monkeypatch.setenv("MPN_TEST_LOG_CHUNKS", chunks)
+    if slots:
+        monkeypatch.setenv("MPN_TEST_DECODE_SLOTS", slots)
+    maze = synth.dfs_maze(512, 512, 62)
+    cases = [rand_case(700, 900, 0.3, 5, 1, 61)[:2], (maze, synth.sample_free(maze, 3, 62))]
+    for m, t in cases:
+        d, L = oracle.bfs(m, t)
+        for bits in (16, 32):
+            if bits == 16 and L > 65534:
+                continue
+            with pkg.Planner(m, bits) as pl:
+                pl.set_tuning(0, 16)
+                assert pl.propagate(t) == L
+                got = pl.distances()
+            assert np.array_equal(widen(got), d)
+
+
 def test_autotune_records_choice_and_stays_exact():
     m, t, s = rand_case(1500, 1400, 0.3, 6, 40, 77)
     with pkg.Planner(m) as pl:

@@ -141,7 +141,7 @@ struct mpn_ctx {
     cudaStream_t stream = nullptr;
 
     DevBuf free_bits, state, dist, ctl, tiles, mask_stage, log;
-    DevBuf targets, starts, offsets, status, cells, activity;
+    DevBuf targets, starts, offsets, status, cells, activity, order;
 
     int variant = 0, depth = 32;
     bool auto_tune = true;
@@ -737,9 +737,14 @@ static mpn_status trace_any(mpn_ctx *c, const uint32_t *starts, int32_t n, uint6
     if (euclid)
         MPN_TRY(launch_euclid(c->grid(), c->dist_bits, ds, n, (uint64_t *)c->offsets.p,
                               (const int8_t *)c->status.p, dcells, true, c->stream, &ctl->err));
-    else
+    else {
+        // scratch for the longest-first walk order (no order if it cannot be had)
+        uint32_t *ord = nullptr;
+        if (c->order.ensure((size_t)n * sizeof(uint32_t)) == cudaSuccess) ord = (uint32_t *)c->order.p;
+        else cudaGetLastError();
         MPN_TRY(launch_trace(c->grid(), c->dist_bits, ds, n, (const uint64_t *)c->offsets.p,
-                             (const int8_t *)c->status.p, dcells, c->stream, &ctl->err));
+                             (const int8_t *)c->status.p, dcells, ord, c->stream, &ctl->err));
+    }
     MPN_TRY(cudaEventRecord(c->ev[5], c->stream));
     c->ev_trace = true;
     if (total > 0 && !cells_dev) MPN_TRY(copy_out(c, cells, dcells, (size_t)total * sizeof(uint32_t)));
@@ -865,7 +870,7 @@ void mpn_destroy(mpn_ctx *c) {
     if (c->out_pending && cudaEventSynchronize(c->ev_out) != cudaSuccess) cudaGetLastError();
     DevBuf *bufs[] = {&c->free_bits, &c->state, &c->log, &c->dist, &c->ctl, &c->tiles,
                       &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
-                      &c->cells, &c->activity};
+                      &c->cells, &c->activity, &c->order};
     for (DevBuf *b : bufs) b->release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);

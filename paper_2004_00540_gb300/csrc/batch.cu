@@ -728,7 +728,7 @@ static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t 
     g.P = m.P;
     return launch_trace(g, m.dist_bits, (const uint32_t *)(res + m.st_o), m.ns,
                         (const uint64_t *)(res + m.off_o), (const int8_t *)(res + m.sts_o), cells,
-                        st, &b->d_bc->c.err);
+                        nullptr, st, &b->d_bc->c.err);
 }
 
 // Wait for the stream, then trace every grid that converged in the last round.

@@ -5,11 +5,18 @@
 // (0,-1), (0,1), (1,-1), (1,0), (1,1).
 //
 // One warp per start. The walk is a chain of dependent steps, so its cost is
-// load latency, not bandwidth: the warp loads a 32 x 32 window of the distance
-// plane around the current cell with 32 coalesced row loads (one per lane per
-// row), then takes every step it can inside the window from shared memory
-// (eight lanes test the eight neighbours, a ballot picks the first), and only
-// reloads when the walk reaches the window's edge.
+// load latency, not bandwidth: the warp loads a window of the distance plane
+// around the current cell, then takes every step it can inside the window from
+// shared memory (eight lanes test the eight neighbours, a ballot picks the
+// first), and only reloads when the walk reaches the window's edge. uint32
+// planes use 64 x 64 windows filled with asynchronous 4-byte copies (all 128
+// per lane in flight at once, no registers held): a long walk crosses about
+// half as many windows as with 32 x 32 ones, each about one memory round trip.
+// Fewer such walks fit on the GPU at once, so the walks are taken longest
+// first (k_order) and the longest one starts at once. uint16 planes use
+// 32 x 32 windows of coalesced row loads.
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 #include "mpn_internal.cuh"
@@ -18,9 +25,62 @@ namespace mpn {
 
 namespace {
 
-constexpr int kWin = 32;          // window side (cells)
+constexpr int kWin = 32;          // window side (cells) of the Euclidean walk
 constexpr int kWinPitch = 33;     // padded row pitch (bank spread)
 constexpr int kTraceWarps = 4;    // warps per block
+
+// walk windows: side, and warps per block (static shared memory <= 48 KB)
+template <typename DT> struct TraceWin {
+    static constexpr int side = 32, warps = 4;
+};
+template <> struct TraceWin<uint32_t> {
+    static constexpr int side = 64, warps = 2;
+};
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Walk order, longest path first: a bitonic sort of {~length, index} keys in
+// shared memory by one block (n <= kOrderMax; the sizes come from the scanned
+// offsets).
+constexpr int kOrderMax = 8192;
+
+__global__ void __launch_bounds__(1024) k_order(const uint64_t *__restrict__ offsets, int n, int m,
+                                                uint32_t *__restrict__ order) {
+    extern __shared__ unsigned long long key[];   // m = next power of two >= n
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        unsigned long long k = ~0ull;
+        if (i < n) {
+            const uint64_t len = offsets[i + 1] - offsets[i];
+            const uint32_t l32 = len > 0xffffffffull ? 0xffffffffu : (uint32_t)len;
+            k = ((unsigned long long)(~l32) << 32) | (uint32_t)i;
+        }
+        key[i] = k;
+    }
+    __syncthreads();
+    for (int size = 2; size <= m; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long a = key[i], b = key[j];
+                    if ((a > b) == up) {
+                        key[i] = b;
+                        key[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (uint32_t)key[i];
+}
 
 template <typename DT>
 __global__ void k_lengths(GridDev g, const uint32_t *__restrict__ starts, int n,
@@ -102,15 +162,18 @@ __global__ void k_scan(uint64_t *a, int n) {
 // the walk ends at (the target reached) to ends[i] and the start's distance
 // to ends_d[i] (0xFFFFFFFF for both when the start has no path).
 template <typename DT, bool CELLS>
-__global__ void __launch_bounds__(kTraceWarps * 32)
+__global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
     k_trace(GridDev g, const uint32_t *__restrict__ starts, int n,
             const uint64_t *__restrict__ offsets, const int8_t *__restrict__ status,
             uint32_t *__restrict__ cells, uint32_t *__restrict__ ends, uint32_t *__restrict__ ends_d,
-            uint32_t *err) {
-    __shared__ DT win[kTraceWarps][kWin * kWinPitch];
+            uint32_t *err, const uint32_t *__restrict__ order) {
+    constexpr int kW = TraceWin<DT>::side, kP = kW + 1, NWp = TraceWin<DT>::warps;
+    __shared__ DT win[NWp][kW * kP];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int i = blockIdx.x * kTraceWarps + wl;
-    if (i >= n) return;                         // whole warp leaves together
+    const int slot = blockIdx.x * NWp + wl;
+    if (slot >= n) return;                      // whole warp leaves together
+    const int i = order ? (int)order[slot] : slot;
+    if (i < 0 || i >= n) return;
     if (status[i] != MPN_PATH_OK) {
         if (!CELLS && lane == 0) {
             ends[i] = 0xffffffffu;
@@ -124,6 +187,12 @@ __global__ void __launch_bounds__(kTraceWarps * 32)
     // neighbour of lane q (q < 8) in the tie-break order
     const int my_dy = (lane < 3) ? -1 : (lane < 5 ? 0 : 1);
     const int my_dx = (lane == 0 || lane == 3 || lane == 5) ? -1 : ((lane == 1 || lane == 6) ? 0 : 1);
+    // two-step lookahead: this lane's first step q1 = lane / 4 and second
+    // steps q2 = lane % 4, lane % 4 + 4 (offsets from the same packed tables)
+    const int q1l = lane >> 2, q2a = lane & 3, q2b = q2a + 4;
+    const int dy1 = (int)((0xa940u >> (2 * q1l)) & 3u) - 1, dx1 = (int)((0x9224u >> (2 * q1l)) & 3u) - 1;
+    const int dy2a = (int)((0xa940u >> (2 * q2a)) & 3u) - 1, dx2a = (int)((0x9224u >> (2 * q2a)) & 3u) - 1;
+    const int dy2b = (int)((0xa940u >> (2 * q2b)) & 3u) - 1, dx2b = (int)((0x9224u >> (2 * q2b)) & 3u) - 1;
 
     uint32_t c = starts[i];
     uint64_t o = CELLS ? offsets[i] : 0ull;
@@ -134,25 +203,76 @@ __global__ void __launch_bounds__(kTraceWarps * 32)
     int ddy = 0, ddx = 0;   // how far the walk moved in the last window
     while (d > 0) {
         // the next window reaches further in the direction the walk has been
-        // heading: along an axis on which it moved at least kWin / 4 cells in
+        // heading: along an axis on which it moved at least kW / 4 cells in
         // the last window, the current cell sits a quarter window in from the
         // trailing edge; otherwise it is centred
-        const int oy = ddy >= kWin / 4 ? kWin / 4 : (ddy <= -kWin / 4 ? kWin - 1 - kWin / 4 : kWin / 2);
-        const int ox = ddx >= kWin / 4 ? kWin / 4 : (ddx <= -kWin / 4 ? kWin - 1 - kWin / 4 : kWin / 2);
+        const int oy = ddy >= kW / 4 ? kW / 4 : (ddy <= -kW / 4 ? kW - 1 - kW / 4 : kW / 2);
+        const int ox = ddx >= kW / 4 ? kW / 4 : (ddx <= -kW / 4 ? kW - 1 - kW / 4 : kW / 2);
         const int wy0 = cy - oy, wx0 = cx - ox;
-        const int x = wx0 + lane;
+        if (sizeof(DT) == 4) {
+#pragma unroll 4
+            for (int r = 0; r < kW; ++r) {
+                const int y = wy0 + r;
+#pragma unroll
+                for (int u = 0; u < kW / 32; ++u) {
+                    const int x = wx0 + 32 * u + lane;
+                    DT *sp = wb + r * kP + 32 * u + lane;
+                    if (y >= 0 && y < g.H && x >= 0 && x < g.W) cp_async4(sp, dist + (size_t)y * g.W + x);
+                    else *sp = INF;
+                }
+            }
+            cp_async_wait_all();
+        } else {
+            const int x = wx0 + lane;
 #pragma unroll 8
-        for (int r = 0; r < kWin; ++r) {
-            const int y = wy0 + r;
-            DT v = INF;
-            if (y >= 0 && y < g.H && x >= 0 && x < g.W) v = dist[(size_t)y * g.W + x];
-            wb[r * kWinPitch + lane] = v;
+            for (int r = 0; r < kW; ++r) {
+                const int y = wy0 + r;
+                DT v = INF;
+                if (y >= 0 && y < g.H && x >= 0 && x < g.W) v = dist[(size_t)y * g.W + x];
+                wb[r * kP + lane] = v;
+            }
         }
         __syncwarp();
         int ly = oy, lx = ox;
-        while (d > 0 && ly >= 1 && ly <= kWin - 2 && lx >= 1 && lx <= kWin - 2) {
+        while (d > 0 && ly >= 1 && ly <= kW - 2 && lx >= 1 && lx <= kW - 2) {
+            if (d >= 2 && ly >= 2 && ly <= kW - 3 && lx >= 2 && lx <= kW - 3) {
+                // two steps at once: lane L tests first step q1 = L / 4 (a
+                // d - 1 neighbour) and second steps q2 = L % 4 and L % 4 + 4
+                // from there (d - 2 neighbours); the first valid q1 in
+                // tie-break order, then its first valid q2, are the two steps
+                // the single-step rule takes
+                const int y1 = ly + dy1, x1 = lx + dx1;
+                const bool a = (uint32_t)wb[y1 * kP + x1] == d - 1u;
+                const bool b0 = (uint32_t)wb[(y1 + dy2a) * kP + x1 + dx2a] == d - 2u;
+                const bool b1 = (uint32_t)wb[(y1 + dy2b) * kP + x1 + dx2b] == d - 2u;
+                const unsigned m1 = __ballot_sync(0xffffffffu, a);
+                const unsigned ma = __ballot_sync(0xffffffffu, a && b0);
+                const unsigned mb = __ballot_sync(0xffffffffu, a && b1);
+                if (!m1) {                      // not a distance plane: give up on this path
+                    if (lane == 0) atomicOr(err, ERR_TRACE);
+                    return;
+                }
+                const int g1 = (__ffs(m1) - 1) & ~3;   // 4 * q1
+                const unsigned m2 = ((ma >> g1) & 0xfu) | (((mb >> g1) & 0xfu) << 4);
+                if (!m2) {
+                    if (lane == 0) atomicOr(err, ERR_TRACE);
+                    return;
+                }
+                const int q1 = g1 >> 2, q2 = __ffs(m2) - 1;
+                const int ly1 = ly + (int)((0xa940u >> (2 * q1)) & 3u) - 1;
+                const int lx1 = lx + (int)((0x9224u >> (2 * q1)) & 3u) - 1;
+                ly = ly1 + (int)((0xa940u >> (2 * q2)) & 3u) - 1;
+                lx = lx1 + (int)((0x9224u >> (2 * q2)) & 3u) - 1;
+                d -= 2u;
+                if (CELLS && lane == 0) {
+                    cells[o + 1] = (uint32_t)((wy0 + ly1) * g.W + (wx0 + lx1));
+                    cells[o + 2] = (uint32_t)((wy0 + ly) * g.W + (wx0 + lx));
+                }
+                o += 2;
+                continue;
+            }
             bool hit = false;
-            if (lane < 8) hit = (uint32_t)wb[(ly + my_dy) * kWinPitch + lx + my_dx] == d - 1u;
+            if (lane < 8) hit = (uint32_t)wb[(ly + my_dy) * kP + lx + my_dx] == d - 1u;
             const unsigned m = __ballot_sync(0xffffffffu, hit);
             if (!m) {                      // not a distance plane: give up on this path
                 if (lane == 0) atomicOr(err, ERR_TRACE);
@@ -317,18 +437,48 @@ cudaError_t launch_scan(uint64_t *offsets, int n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// the largest shared-memory carveout for the 64 x 64 windows, and the sort's
+// shared memory
+static cudaError_t trace_attributes() {
+    static std::once_flag once;
+    static cudaError_t e = cudaSuccess;
+    std::call_once(once, [] {
+        const void *fns[2] = {(const void *)k_trace<uint32_t, true>, (const void *)k_trace<uint32_t, false>};
+        for (const void *f : fns)
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kOrderMax * (int)sizeof(unsigned long long));
+    });
+    return e;
+}
+
 cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
                          const uint64_t *offsets, const int8_t *status, uint32_t *cells,
-                         cudaStream_t st, uint32_t *err) {
+                         uint32_t *order, cudaStream_t st, uint32_t *err) {
     if (n <= 0) return cudaSuccess;
-    const int nb = (n + kTraceWarps - 1) / kTraceWarps;
-    count_launch();
-    if (dist_bits == 16)
-        k_trace<uint16_t, true><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, offsets, status, cells,
-                                                                 nullptr, nullptr, err);
-    else
-        k_trace<uint32_t, true><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, offsets, status, cells,
-                                                                 nullptr, nullptr, err);
+    if (cudaError_t e = trace_attributes()) return e;
+    if (dist_bits == 16) {
+        constexpr int w = TraceWin<uint16_t>::warps;
+        count_launch();
+        k_trace<uint16_t, true><<<(n + w - 1) / w, w * 32, 0, st>>>(g, starts, n, offsets, status, cells,
+                                                                    nullptr, nullptr, err, nullptr);
+    } else {
+        constexpr int w = TraceWin<uint32_t>::warps;
+        const uint32_t *ord = nullptr;
+        if (order && n <= kOrderMax) {
+            int m = 1;
+            while (m < n) m <<= 1;
+            count_launch();
+            k_order<<<1, 1024, (size_t)m * sizeof(unsigned long long), st>>>(offsets, n, m, order);
+            ord = order;
+        }
+        count_launch();
+        k_trace<uint32_t, true><<<(n + w - 1) / w, w * 32, 0, st>>>(g, starts, n, offsets, status, cells,
+                                                                    nullptr, nullptr, err, ord);
+    }
     return cudaGetLastError();
 }
 
@@ -336,14 +486,17 @@ cudaError_t launch_nearest(const GridDev &g, int dist_bits, const uint32_t *star
                            const int8_t *status, uint32_t *ends, uint32_t *ends_d, cudaStream_t st,
                            uint32_t *err) {
     if (n <= 0) return cudaSuccess;
-    const int nb = (n + kTraceWarps - 1) / kTraceWarps;
+    if (cudaError_t e = trace_attributes()) return e;
     count_launch();
-    if (dist_bits == 16)
-        k_trace<uint16_t, false><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, nullptr, status, nullptr,
-                                                                  ends, ends_d, err);
-    else
-        k_trace<uint32_t, false><<<nb, kTraceWarps * 32, 0, st>>>(g, starts, n, nullptr, status, nullptr,
-                                                                  ends, ends_d, err);
+    if (dist_bits == 16) {
+        constexpr int w = TraceWin<uint16_t>::warps;
+        k_trace<uint16_t, false><<<(n + w - 1) / w, w * 32, 0, st>>>(g, starts, n, nullptr, status, nullptr,
+                                                                     ends, ends_d, err, nullptr);
+    } else {
+        constexpr int w = TraceWin<uint32_t>::warps;
+        k_trace<uint32_t, false><<<(n + w - 1) / w, w * 32, 0, st>>>(g, starts, n, nullptr, status, nullptr,
+                                                                     ends, ends_d, err, nullptr);
+    }
     return cudaGetLastError();
 }
 

@@ -47,4 +47,7 @@ def test_argument_errors_need_no_gpu():
     assert L.mpn_create(buf, 0, 4, 0, None, ctypes.byref(out)) == pkg.MPN_EINVAL
     assert L.mpn_create(buf, 4, 4, 8, None, ctypes.byref(out)) == pkg.MPN_EINVAL
     assert L.mpn_sync(None) == pkg.MPN_EINVAL
+    assert L.mpn_get_distances(None, buf, 0) == pkg.MPN_EINVAL
+    assert L.mpn_get_distances_async(None, buf, None) == pkg.MPN_EINVAL
+    assert L.mpn_trace(None, None, 0, None, None, 0, None) == pkg.MPN_EINVAL
     assert L.mpn_launch_count() == 0

@@ -150,8 +150,8 @@ cudaError_t launch_trace_lengths(const GridDev &g, int dist_bits, const uint32_t
                                  uint64_t *lens_or_offsets, int8_t *status, Ctl *ctl,
                                  cudaStream_t st);
 cudaError_t launch_scan(uint64_t *offsets, int n, cudaStream_t st);
-// order: n words of scratch for the longest-first walk order (uint32 planes,
-// n <= 8192), or null for the starts' own order
+// order: n words of scratch for the longest-first walk order (uint32 planes),
+// or null for the starts' own order
 cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
                          const uint64_t *offsets, const int8_t *status, uint32_t *cells,
                          uint32_t *order, cudaStream_t st, uint32_t *err);

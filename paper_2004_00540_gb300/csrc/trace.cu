@@ -13,7 +13,7 @@
 // per lane in flight at once, no registers held): a long walk crosses about
 // half as many windows as with 32 x 32 ones, each about one memory round trip.
 // Fewer such walks fit on the GPU at once, so the walks are taken longest
-// first (k_order) and the longest one starts at once. uint16 planes use
+// first (k_order) and the longest ones start at once. uint16 planes use
 // 32 x 32 windows of coalesced row loads.
 #include <mutex>
 
@@ -45,41 +45,32 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Walk order, longest path first: a bitonic sort of {~length, index} keys in
-// shared memory by one block (n <= kOrderMax; the sizes come from the scanned
-// offsets).
-constexpr int kOrderMax = 8192;
-
-__global__ void __launch_bounds__(1024) k_order(const uint64_t *__restrict__ offsets, int n, int m,
+// Walk order, longest paths first: one block sorts the starts into 33
+// buckets by the bit length of their path length (a shared-memory count, a
+// prefix, a scatter), so the walks of the longest bucket come first. Within a
+// bucket the order is whatever the atomics give; it only affects speed.
+__global__ void __launch_bounds__(1024) k_order(const uint64_t *__restrict__ offsets, int n,
                                                 uint32_t *__restrict__ order) {
-    extern __shared__ unsigned long long key[];   // m = next power of two >= n
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        unsigned long long k = ~0ull;
-        if (i < n) {
-            const uint64_t len = offsets[i + 1] - offsets[i];
-            const uint32_t l32 = len > 0xffffffffull ? 0xffffffffu : (uint32_t)len;
-            k = ((unsigned long long)(~l32) << 32) | (uint32_t)i;
+    __shared__ unsigned cnt[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    auto bucket = [&](int i) {   // 0: length >= 2^31 ... 32: length 0
+        const uint64_t len = offsets[i + 1] - offsets[i];
+        const uint32_t l32 = len > 0xffffffffull ? 0xffffffffu : (uint32_t)len;
+        return __clz(l32);
+    };
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[bucket(i)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned a = 0u;
+        for (int k = 0; k < 33; ++k) {
+            const unsigned c = cnt[k];
+            cnt[k] = a;
+            a += c;
         }
-        key[i] = k;
     }
     __syncthreads();
-    for (int size = 2; size <= m; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    const bool up = (i & size) == 0;
-                    const unsigned long long a = key[i], b = key[j];
-                    if ((a > b) == up) {
-                        key[i] = b;
-                        key[j] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) order[i] = (uint32_t)key[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&cnt[bucket(i)], 1u)] = (uint32_t)i;
 }
 
 template <typename DT>
@@ -437,8 +428,7 @@ cudaError_t launch_scan(uint64_t *offsets, int n, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// the largest shared-memory carveout for the 64 x 64 windows, and the sort's
-// shared memory
+// the largest shared-memory carveout for the 64 x 64 windows
 static cudaError_t trace_attributes() {
     static std::once_flag once;
     static cudaError_t e = cudaSuccess;
@@ -448,9 +438,6 @@ static cudaError_t trace_attributes() {
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          cudaSharedmemCarveoutMaxShared);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kOrderMax * (int)sizeof(unsigned long long));
     });
     return e;
 }
@@ -468,11 +455,9 @@ cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts
     } else {
         constexpr int w = TraceWin<uint32_t>::warps;
         const uint32_t *ord = nullptr;
-        if (order && n <= kOrderMax) {
-            int m = 1;
-            while (m < n) m <<= 1;
+        if (order) {
             count_launch();
-            k_order<<<1, 1024, (size_t)m * sizeof(unsigned long long), st>>>(offsets, n, m, order);
+            k_order<<<1, 1024, 0, st>>>(offsets, n, order);
             ord = order;
         }
         count_launch();

@@ -184,6 +184,10 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
     const int dy1 = (int)((0xa940u >> (2 * q1l)) & 3u) - 1, dx1 = (int)((0x9224u >> (2 * q1l)) & 3u) - 1;
     const int dy2a = (int)((0xa940u >> (2 * q2a)) & 3u) - 1, dx2a = (int)((0x9224u >> (2 * q2a)) & 3u) - 1;
     const int dy2b = (int)((0xa940u >> (2 * q2b)) & 3u) - 1, dx2b = (int)((0x9224u >> (2 * q2b)) & 3u) - 1;
+    // the same as offsets in the window (row pitch kP), from the current cell
+    const int off1 = dy1 * kP + dx1;
+    const int off2a = off1 + dy2a * kP + dx2a, off2b = off1 + dy2b * kP + dx2b;
+    const int my_off = my_dy * kP + my_dx;
 
     uint32_t c = starts[i];
     uint64_t o = CELLS ? offsets[i] : 0ull;
@@ -232,10 +236,10 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
                 // from there (d - 2 neighbours); the first valid q1 in
                 // tie-break order, then its first valid q2, are the two steps
                 // the single-step rule takes
-                const int y1 = ly + dy1, x1 = lx + dx1;
-                const bool a = (uint32_t)wb[y1 * kP + x1] == d - 1u;
-                const bool b0 = (uint32_t)wb[(y1 + dy2a) * kP + x1 + dx2a] == d - 2u;
-                const bool b1 = (uint32_t)wb[(y1 + dy2b) * kP + x1 + dx2b] == d - 2u;
+                const DT *cur = wb + ly * kP + lx;
+                const bool a = (uint32_t)cur[off1] == d - 1u;
+                const bool b0 = (uint32_t)cur[off2a] == d - 2u;
+                const bool b1 = (uint32_t)cur[off2b] == d - 2u;
                 const unsigned m1 = __ballot_sync(0xffffffffu, a);
                 const unsigned ma = __ballot_sync(0xffffffffu, a && b0);
                 const unsigned mb = __ballot_sync(0xffffffffu, a && b1);
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
                 continue;
             }
             bool hit = false;
-            if (lane < 8) hit = (uint32_t)wb[(ly + my_dy) * kP + lx + my_dx] == d - 1u;
+            if (lane < 8) hit = (uint32_t)wb[ly * kP + lx + my_off] == d - 1u;
             const unsigned m = __ballot_sync(0xffffffffu, hit);
             if (!m) {                      // not a distance plane: give up on this path
                 if (lane == 0) atomicOr(err, ERR_TRACE);

@@ -20,7 +20,11 @@
  *  - Every call returns an mpn_status; nothing aborts or exits.
  *  - Pointer arguments documented "host or device" are classified with
  *    cudaPointerGetAttributes: device (and managed) memory is read in place,
- *    anything else is treated as host memory and copied.
+ *    anything else is treated as host memory and copied. Path, offset,
+ *    status and nearest-target results bound for page-locked host memory are
+ *    stored there by a small kernel (not a copy engine, whose device-to-host
+ *    transfers queue behind other streams' large downloads), so such
+ *    buffers must be writable by the device (not registered read-only).
  *  - Work is ordered on the context's stream (mpn_create's stream, or
  *    mpn_set_stream). A context is not thread-safe; separate contexts are
  *    independent. The caller owns every buffer it passes; the context owns

@@ -8,7 +8,9 @@ starts): encode the uint8 mask to bits, propagate the activity wave to
 convergence, trace all 4000 paths. Inputs are resident in HBM when the timed
 region starts (value); e2e repeats the step through the C ABI from pinned host
 buffers, with the mask upload and the distance-map and path downloads inside
-the timed region.
+the timed region, as a stream of solves pipelined over two contexts (one
+solve's download overlapping the next one's upload and kernels); e2e.serial
+runs them one at a time.
 
 metric: effective cell-updates/s = H * W * L / t, L = the number of layers the
 paper's network needs (the largest finite distance), as in the paper's O(N L)

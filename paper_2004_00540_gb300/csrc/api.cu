@@ -516,7 +516,8 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     // itself, so the size only affects speed). The TMA-staged variant writes
     // its distances itself.
     const uint64_t log_entries = c->plane_words() * 3 / 2 + (uint64_t)c->blocks * kLogChunk;
-    uint32_t log_chunks = variant_desc(c->variant).tma
+    // (a visit's header and entries must fit one chunk; every compiled tiling does)
+    uint32_t log_chunks = (variant_desc(c->variant).tma || (uint64_t)c->TY * c->TXW + 1 > kLogChunk)
                               ? 0u : (uint32_t)((log_entries + kLogChunk - 1) / kLogChunk);
     // test hooks for the fallback paths: a smaller pool (MPN_TEST_LOG_CHUNKS;
     // 0 = no log), fewer decode slots (MPN_TEST_DECODE_SLOTS)

@@ -266,6 +266,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
 // Indices outside the pool end the tile's walk (defensive; the propagation
 // never writes one).
 constexpr int kDecodeBatch = 64;
+static_assert(kDecodeBatch >= (int)kTileSlots && kDecodeBatch == 64,
+              "the first batch holds every slot; the count prefix is two warps wide");
 
 __device__ __forceinline__ uint32_t spread_nibble(uint32_t n) {   // bit i -> bit 8 i
     return (n * 0x204081u) & 0x01010101u;

@@ -41,6 +41,11 @@ import synth  # noqa: E402
 METRIC = "effective cell-updates/sec"
 UNIT = "cell-updates/s"
 BYTES_PER_UPDATE_U32 = 8.125      # read the mask bit, read and write the uint32 distance
+# Floor of one propagation: read the packed mask once (1/8 B per cell) and
+# write the uint32 distance plane once (4 B per cell); every other byte a
+# kernel moves is overhead of its design.
+FLOOR_BYTES_PER_CELL_U32 = 4.125
+L2_NOTE = "inputs larger than L2 (uint8 mask 537 MB + uint32 distance plane 2.15 GB per step)"
 
 
 def parse():
@@ -56,6 +61,8 @@ def parse():
     ap.add_argument("--depth", type=int, default=32)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-maze batched/served part")
+    ap.add_argument("--no-per-config", action="store_true",
+                    help="skip the 64^2, 1024^2-maze and 4096^2-maze single-grid timings")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--plain-sample", type=int, default=32,
                     help="mazes timed with one launch per layer (the slow baseline)")
@@ -238,29 +245,90 @@ def cpu_baseline(w, sample_side=23170):
     return out
 
 
+def workload_config(w, layers: int, path_cells: int, world: int) -> dict:
+    """The `config` of a bench line: the workload alone (both arms print the
+    same dict for the same work; tiling choices go elsewhere)."""
+    return {"workload": w.name, "H": w.H, "W": w.W, "targets": int(w.targets.size),
+            "starts": int(w.starts.size), "layers": int(layers), "path_cells": int(path_cells),
+            "step": "encode + propagate + trace", "parallelism": f"replicas x{world}",
+            "l2": L2_NOTE}
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands (single-thread BFS +
+    trace) on the same full workload as a step of our arm. Its W warm-up
+    steps run on a 4096 x 4096 window (untimed; only the timed steps count),
+    so that K = 20 timed steps of about 10 s each end within a few minutes."""
     if rank != 0:
         return 0
+    import oracle
     w = workload(args.side)
-    s = crop(w, min(8192, w.H))
-    times, L = [], 0
-    for i in range(args.warmup + args.steps):
-        dt, L = time_oracle(s)
-        if i >= args.warmup:
-            times.append(dt)
+    warm = crop(w, min(4096, w.H))
+    for _ in range(args.warmup):
+        time_oracle(warm)
+    times, L, cells = [], 0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        d, L = oracle.bfs(w.mask, w.targets)
+        off, _, _ = oracle.trace(w.mask, d, w.starts)
+        times.append(time.perf_counter() - t0)
+        cells = int(off[-1])
     t = sum(times)
-    v = s.H * s.W * L * len(times) / t
+    v = w.H * w.W * L * len(times) / t
+    sample = (f"the full {w.H}x{w.W} workload, {w.targets.size} targets, {w.starts.size} starts "
+              f"(L={L}), every timed step; warm-up steps on its top-left {warm.H}x{warm.W} window")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic",
-            "config": {"workload": w.name, "sample": f"top-left {s.H}x{s.W} window", "layers": L},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"top-left {s.H}x{s.W} window of {w.name}, "
-                                       f"{s.targets.size} targets, {s.starts.size} starts"},
+            "data": "synthetic", "config": workload_config(w, L, cells, 1),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_per_config(pkg, torch, reps: int = 5):
+    """The single-grid configurations besides the headline one (64 x 64
+    Bernoulli, the 1024 x 1024 DFS maze, the 4096 x 4096 maze with 20 % of its
+    walls opened), device-resident: propagate + trace, best of `reps` after a
+    warm-up, each checked against the CPU oracle once (layer count and path
+    cell total)."""
+    import oracle
+    out = {}
+    for w in (synth.c1_small(), synth.c2_maze(), synth.c3_maze_open()):
+        m = torch.from_numpy(w.mask).cuda()
+        t = torch.from_numpy(w.targets.view(np.int32)).cuda()
+        s = torch.from_numpy(w.starts.view(np.int32)).cuda()
+        n = w.starts.size
+        with pkg.Planner(m, w.dist_bits) as pl:
+            L = pl.propagate(t)
+            off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+            pkg.mpn_trace_lengths(pl.ctx, s, off)
+            total = int(off[-1].item())
+            cells = torch.zeros(max(total, 1), dtype=torch.int32, device="cuda")
+            status = torch.zeros(n, dtype=torch.int8, device="cuda")
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            best, prop, trace = None, None, None
+            for r in range(reps + 1):
+                torch.cuda.synchronize()
+                ev0.record()
+                pkg.mpn_propagate(pl.ctx, t, 0, wait=False)
+                pkg.mpn_trace(pl.ctx, s, off, cells, total, status)
+                ev1.record()
+                ev1.synchronize()
+                ms = ev0.elapsed_time(ev1)
+                st = pl.stats()
+                if r and (best is None or ms < best):
+                    best, prop, trace = ms, st["ms_propagate"], st["ms_trace"]
+        od, oL = oracle.bfs(w.mask, w.targets)
+        ooff, _, _ = oracle.trace(w.mask, od, w.starts)
+        out[w.name] = {"H": w.H, "W": w.W, "layers": int(L), "dist_bits": w.dist_bits,
+                       "step_ms": best, "propagate_ms": prop, "trace_ms": trace,
+                       "effective_cell_updates_per_s": w.H * w.W * L / (prop * 1e-3),
+                       "paths": int(n), "path_cells": total, "sweeps": st["sweeps"],
+                       "variant": st["variant"], "depth": st["depth"],
+                       "equals_oracle": bool(L == oL and total == int(ooff[-1]))}
+    return out
 
 
 def run_batched(args, pkg, torch):
@@ -477,19 +545,26 @@ def main():
         pg.barrier()
     prop_avg = sum(prop_ms) / len(prop_ms)
 
-    # roofline of the dominant kernel: the persistent propagation kernel and
-    # the activation-log decode that completes its distance plane (the
-    # context's propagate events bracket both)
+    # roofline of the dominant kernel pair: the persistent propagation kernel
+    # and the activation-log decode that completes its distance plane (the
+    # context's propagate events bracket both). Algorithmic bytes = the
+    # floor of a propagation (packed mask read once, uint32 plane written
+    # once); the dense N * L equivalent is reported as cell-updates/s only.
     peak, peak_kind = peaks()
-    achieved = units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / 1e9
+    floor_bytes = FLOOR_BYTES_PER_CELL_U32 * H * W
+    achieved = floor_bytes / (prop_avg * 1e-3) / 1e9
     traffic = measured_traffic(w.name, st["variant"], st["depth"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic,
+            "frac": achieved / peak, "traffic": traffic, "floor_bytes": floor_bytes,
             "dram_frac": (traffic / (prop_avg * 1e-3) / (peak * 1e9)) if traffic else None,
+            "traffic_over_floor": (traffic / floor_bytes) if traffic else None,
             "peak_kind": peak_kind,
             "kernel": "k_propagate + k_log_decode", "ms_per_launch": prop_avg,
-            "note": "algorithmic bytes = 8.125 B per effective cell-update (mask bit + uint32 "
-                    "read + write per layer); temporal blocking does each update in registers"}
+            "effective_cell_updates_per_s": units / (prop_avg * 1e-3),
+            "note": "algorithmic bytes per launch = 4.125 B per cell (packed mask bit read once, "
+                    "uint32 distance written once) x H x W; frac = those bytes / launch time / "
+                    "measured copy peak; traffic = ncu DRAM read + write bytes of both kernels "
+                    "per launch"}
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -590,13 +665,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": w.name, "H": H, "W": W, "targets": int(w.targets.size),
-                   "starts": int(n), "layers": int(L), "path_cells": total,
-                   "step": "encode + propagate + trace", "parallelism": f"replicas x{world}",
-                   "variant": st["variant"], "depth": st["depth"], "autotuned": tuned,
-                   "l2": "inputs larger than L2 (uint8 mask 537 MB + uint32 distance plane 2.15 GB per step)"},
+        "config": workload_config(w, L, total, world),
+        "tuning": {"variant": st["variant"], "depth": st["depth"], "autotuned": tuned},
         "propagate": {"ms": prop_avg, "effective_cell_updates_per_s": units / (prop_avg * 1e-3),
-                      "pct_hbm_roofline": 100 * units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3) / (peak * 1e9),
+                      "dense_equivalent_bytes_per_s": units * BYTES_PER_UPDATE_U32 / (prop_avg * 1e-3),
                       "sweeps": st["sweeps"], "tile_visits": st["tile_visits"],
                       "tiles": st["tiles_x"] * st["tiles_y"], "blocks": st["blocks"],
                       "tile_layers_executed_frac": st["tile_layers"] / max(1, st["tile_visits"] * st["depth"]),
@@ -613,6 +685,8 @@ def main():
         pg.destroy_process_group()
     if not args.no_batched and world == 1:
         line["batched"] = run_batched(args, pkg, torch)
+    if not args.no_per_config and world == 1:
+        line["per_config"] = run_per_config(pkg, torch)
     if not args.no_cpu and world == 1:
         line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)

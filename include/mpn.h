@@ -85,17 +85,20 @@ mpn_status mpn_create(const uint8_t *mask, int32_t H, int32_t W, int32_t dist_bi
  * Like mpn_create, from an already packed FREE-cell bit plane: H rows of
  * pitch_words uint32 words; bit b of word w in row y is cell x = 32*w + b,
  * 1 = free. pitch_words >= ceil(W/32); bits at x >= W are ignored. Host or
- * device.
+ * device. Same environment map I_e as mpn_create (Methods, "Input": 0 on free
+ * cells, -maxint on obstacles), given one bit per cell.
  */
 mpn_status mpn_create_packed(const uint32_t *free_bits, int32_t H, int32_t W,
                              int32_t pitch_words, int32_t dist_bits, void *stream,
                              mpn_ctx **out);
 
 /* Re-encode a new H*W uint8 mask of the same size (host or device), keeping
- * all allocations. Invalidates earlier distances. */
+ * all allocations (Methods, "Input": a new environment map I_e for the same
+ * network). Invalidates earlier distances. */
 mpn_status mpn_set_mask(mpn_ctx *ctx, const uint8_t *mask);
 
-/* Bind later work to another stream (a cudaStream_t). */
+/* Bind later work to another stream (a cudaStream_t). No counterpart in the
+ * paper (stream plumbing). */
 mpn_status mpn_set_stream(mpn_ctx *ctx, void *stream);
 
 /*
@@ -126,7 +129,10 @@ mpn_status mpn_propagate_plain(mpn_ctx *ctx, const uint32_t *targets, int32_t n_
 
 /* Copy the distance plane (H*W elements of the context's dtype, row-major)
  * to dst; dst_on_device selects cudaMemcpyDeviceToDevice vs DeviceToHost.
- * Waits for the copy. MPN_ESTATE before the first propagate. */
+ * Waits for the copy. MPN_ESTATE before the first propagate. The plane holds
+ * each cell's first-activation layer d, from which the paper's activity map
+ * is O = L + 1 - d (Methods, "Activity Map Generation"; mpn_get_activity
+ * returns O itself). */
 mpn_status mpn_get_distances(mpn_ctx *ctx, void *dst, int32_t dst_on_device);
 
 /*
@@ -153,9 +159,11 @@ mpn_status mpn_get_activity(mpn_ctx *ctx, uint32_t L, int32_t *dst, int32_t dst_
 
 /*
  * Path lengths only (for sizing): offsets[0] = 0 and offsets[i+1] -
- * offsets[i] = d(start_i) + 1 cells for a reachable start, 0 otherwise.
- * starts: n >= 0 uint32 linear indices, host or device. offsets: n+1 uint64,
- * host. Waits for the GPU.
+ * offsets[i] = d(start_i) + 1 cells for a reachable start, 0 otherwise
+ * (Methods, "Path Reconstruction": a path from a start at distance d takes d
+ * steps, one layer of activity per step). starts: n >= 0 uint32 linear
+ * indices, host or device. offsets: n+1 uint64, host or device. Waits for the
+ * GPU.
  */
 mpn_status mpn_trace_lengths(mpn_ctx *ctx, const uint32_t *starts, int32_t n,
                              uint64_t *offsets);
@@ -205,15 +213,21 @@ mpn_status mpn_nearest_targets(mpn_ctx *ctx, const uint32_t *starts, int32_t n,
                                uint32_t *target, uint32_t *dist);
 
 /* Wait for the context's stream and for its pending asynchronous distance
- * copy (mpn_get_distances_async); report any error the GPU recorded. */
+ * copy (mpn_get_distances_async); report any error the GPU recorded. No
+ * counterpart in the paper (stream plumbing). */
 mpn_status mpn_sync(mpn_ctx *ctx);
 
+/* Free every device and host resource of the context (NULL is a no-op). No
+ * counterpart in the paper (resource plumbing). */
 void mpn_destroy(mpn_ctx *ctx);
 
+/* Name of a status code. No counterpart in the paper. */
 const char *mpn_status_str(mpn_status s);
 
 /*
- * Propagation tiling. variant: index into the compiled tile shapes
+ * Propagation tiling (no counterpart in the paper, which runs one library
+ * max-pool per layer; here k layers of Methods, "Activity Map Generation", run
+ * per tile visit). variant: index into the compiled tile shapes
  * (mpn_variant_info); depth: temporal blocking depth k = layers advanced per
  * tile visit, 1..32 (also the halo width in rows), with region_rows - 2k >= k
  * (the interior must be at least as tall as the halo), else MPN_EINVAL.
@@ -222,7 +236,8 @@ const char *mpn_status_str(mpn_status s);
 mpn_status mpn_set_tuning(mpn_ctx *ctx, int32_t variant, int32_t depth);
 
 /*
- * Autotuner: time every compiled tile shape and every depth in {8, 12, 16,
+ * Autotuner (no counterpart in the paper; its run time depends on L and n,
+ * Results, "Run-time"): time every compiled tile shape and every depth in {8, 12, 16,
  * 24, 32} (where the shape allows it) by propagating from these targets on
  * this context's grid; keep the fastest for the context and record, for the
  * grid's size bucket ceil(log2(max(H, W))), the fastest depth per shape and
@@ -234,7 +249,8 @@ mpn_status mpn_autotune(mpn_ctx *ctx, const uint32_t *targets, int32_t n_targets
                         int32_t *variant, int32_t *depth, float *best_ms);
 
 /* Shape of compiled tile variant v: region rows, region words (32 cells
- * each), threads per block. MPN_EINVAL past the last variant. */
+ * each), threads per block. MPN_EINVAL past the last variant. No counterpart
+ * in the paper. */
 mpn_status mpn_variant_info(int32_t v, int32_t *region_rows, int32_t *region_words,
                             int32_t *threads);
 
@@ -253,14 +269,17 @@ typedef struct {
                                         reached cells in it) the last propagate wrote */
 } mpn_stats;
 
-/* Statistics of the last calls (waits for the GPU). */
+/* Statistics of the last calls (waits for the GPU). layers is the paper's L,
+ * the number of layers the network needs (Methods, "Determining the number of
+ * layers L"); the rest has no counterpart in the paper. */
 mpn_status mpn_get_stats(mpn_ctx *ctx, mpn_stats *out);
 
-/* Number of kernels this library has launched in this process. */
+/* Number of kernels this library has launched in this process. No
+ * counterpart in the paper (measurement). */
 uint64_t mpn_launch_count(void);
 
 /* Text of the last CUDA runtime error behind an MPN_ECUDA / MPN_ENOMEM
- * returned to this host thread ("" if none). */
+ * returned to this host thread ("" if none). No counterpart in the paper. */
 const char *mpn_last_error(void);
 
 /* ------------------------------------------------------------------------
@@ -287,6 +306,12 @@ const char *mpn_last_error(void);
  * graph and replayed; its launch parameters never change because the
  * per-round state lives in device memory. Results are the same as one grid solved
  * alone with mpn_create/mpn_propagate/mpn_trace (bit for bit).
+ *
+ * The paper solves one map per network run and has no batch; each grid of a
+ * batch goes through the same layers (Methods, "Activity Map Generation") and
+ * the same simple path reconstruction (Methods, "Path Reconstruction"). The
+ * batch calls below that only manage memory, tickets and rounds have no
+ * counterpart in the paper.
  * ------------------------------------------------------------------------ */
 typedef struct mpn_batch mpn_batch;
 
@@ -373,14 +398,20 @@ void mpn_batch_destroy(mpn_batch *b);
  * for it to report errors (MPN_EINVAL for a target out of range,
  * MPN_EOBSTACLE for one on an obstacle).
  *
- * Limit: H <= 2048 and W <= 2048; larger grids return MPN_EINVAL. The scratch
- * (bit planes, tile queue, control block; about 2.6 MB) is one fixed device
- * array that every GPU loading this library holds until the process exits.
- * Calls never call cudaMalloc/cudaFree or any allocating routine. The first
- * call on each device looks up that array's device address
- * (cudaGetSymbolAddress), so make it before any stream capture. All calls
- * share the array and each clears what must start at zero; calls whose GPU
- * work overlaps (other streams, other host threads) race on it.
+ * Limit: H <= 2048 and W <= 2048; larger grids return MPN_EINVAL, and so does
+ * a mask, targets or dist pointer that is not memory of the current device.
+ * The scratch (bit planes, tile queue, control block; about 2.6 MB) is one
+ * fixed device array that every GPU on which this library's device code is
+ * loaded holds until the process exits; with lazy module loading (the CUDA
+ * default) that happens at the first use on the device, so the first call
+ * there (or a warm-up call at start-up) is when the footprint grows. Calls
+ * never call cudaMalloc/cudaFree or any allocating routine. The first call on
+ * each device (and the first after a reset of it) looks up that array's device
+ * address (cudaGetSymbolAddress) as its set-up, so make it before any stream
+ * capture. Every call waits for its stream to finish (it reads the GPU's
+ * error word back to the host) before it returns. All calls share the array
+ * and each clears what must start at zero; calls whose GPU work overlaps
+ * (other streams, other host threads) race on it.
  */
 mpn_status mpn_propagate_noalloc(const uint8_t *mask, int32_t H, int32_t W,
                                  const uint32_t *targets, int32_t n_targets,

@@ -176,7 +176,10 @@ def omap(mask, targets, L: int) -> np.ndarray:
 
 def euclid_trace(mask, dist, starts):
     """Euclidean path reconstruction (4-neighbour ascent + straightening).
-    Returns (offsets, cells, status); status 3 = the 4-neighbour walk stalled."""
+    Returns (offsets, cells, status) with the per-start status of trace()
+    (0 path, 1 unreachable, 2 on an obstacle). A walk that finds no next cell
+    can only come from a plane that is not a BFS distance map; the call then
+    raises OracleError(EINVAL)."""
     m = _mask(mask)
     H, W = m.shape
     d = np.ascontiguousarray(dist, np.uint32)

@@ -558,6 +558,17 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     p.log_chunks = log_chunks;
     const uint64_t bound = (max_layers ? (uint64_t)max_layers : (uint64_t)c->H * c->W) / c->depth + 3;
     p.sweep_cap = (uint32_t)(bound < (1u << 22) ? bound : (1u << 22));
+    // test hooks that make the device-side limits run out on purpose (the
+    // kernel then records the error and every block returns):
+    // MPN_TEST_SPIN_LIMIT polls per grid-barrier wait, MPN_TEST_SWEEP_CAP sweeps
+    if (const char *e = getenv("MPN_TEST_SPIN_LIMIT")) {
+        const long v = strtol(e, nullptr, 10);
+        if (v >= 0 && (uint64_t)v < p.spin_limit) p.spin_limit = (uint32_t)v;
+    }
+    if (const char *e = getenv("MPN_TEST_SWEEP_CAP")) {
+        const long v = strtol(e, nullptr, 10);
+        if (v >= 1 && (uint64_t)v < p.sweep_cap) p.sweep_cap = (uint32_t)v;
+    }
     MPN_TRY(launch_seed(dt, n, p, c->dist_bits, c->stream));
     MPN_TRY(cudaEventRecord(c->ev[2], c->stream));   // times the persistent kernel + log decode
     MPN_TRY(launch_propagate(c->variant, c->dist_bits, p, c->blocks, c->stream));

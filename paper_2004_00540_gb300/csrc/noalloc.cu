@@ -7,14 +7,21 @@
 // their own input and output buffers; every piece of scratch this path needs
 // lives in one file-scope device array of fixed size instead.
 //
-// That array belongs to every GPU that loads this library, from load until the
-// process exits (about 2.6 MB). Calls share it and it keeps the last call's
-// contents, so each call clears what must start at zero, and two calls whose
-// GPU work overlaps (different streams, or different host threads) race on it.
+// That array (about 2.6 MB) belongs to every GPU on which this library's
+// device code is loaded, until the process exits. With lazy module loading
+// (the CUDA default) the code and the array are loaded on a device at the
+// first use, which for a caller of this entry point alone is its first call
+// there (the address lookup below): that call, or a warm-up call made at
+// start-up, is when the footprint grows. Calls share the array and it keeps
+// the last call's contents, so each call clears what must start at zero, and
+// two calls whose GPU work overlaps (different streams, or different host
+// threads) race on it.
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "mpn_internal.cuh"
 
@@ -42,23 +49,73 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes
 
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
-unsigned char *g_addr[kMaxDevices] = {};   // device address of the scratch, per device
+// Device address of the scratch, per device, with the id of the context it
+// was looked up in: a device reset ends that context and the array comes back
+// at a new address in the next one, so the lookup is repeated when the
+// current context's id (unique for the life of the process) changes.
+struct ScratchAddr {
+    unsigned long long ctx_id = 0;
+    unsigned char *addr = nullptr;
+};
+ScratchAddr g_addr[kMaxDevices];
 
-// Once per device, with that device current: look up the array's address.
-cudaError_t scratch_address(unsigned char **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+template <typename F>
+F driver_fn(const char *name, int version) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &f, version, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        return (F)f;
+    cudaGetLastError();
+    return nullptr;
+}
+
+// id of the current context; 0 when there is none yet
+bool current_ctx_id(unsigned long long *id) {
+    static PFN_cuCtxGetCurrent_v4000 get_ctx = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        get_ctx = driver_fn<PFN_cuCtxGetCurrent_v4000>("cuCtxGetCurrent", 4000);
+        get_id = driver_fn<PFN_cuCtxGetId_v12000>("cuCtxGetId", 12000);
+    });
+    if (!get_ctx || !get_id) return false;
+    CUcontext ctx = nullptr;
+    if (get_ctx(&ctx) != CUDA_SUCCESS) return false;
+    *id = 0;
+    return !ctx || get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Set-up, once per device (and again after a reset of it), with that device
+// current: look up the array's device address. In host code the array's name
+// is only a stand-in; kernels must get this address.
+cudaError_t scratch_address(int dev, unsigned char **out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long id = 0;   // 0: the runtime has not set the device up yet
+    if (!current_ctx_id(&id)) return cudaErrorDeviceUninitialized;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    ScratchAddr &a = g_addr[dev];
+    if (!id || a.ctx_id != id || !a.addr) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // sets the context up if needed
         if (e != cudaSuccess) return e;
-        g_addr[dev] = static_cast<unsigned char *>(p);
+        if (!id && (!current_ctx_id(&id) || !id)) return cudaErrorDeviceUninitialized;
+        a.ctx_id = id;
+        a.addr = static_cast<unsigned char *>(p);
     }
-    *out = g_addr[dev];
+    *out = a.addr;
     return cudaSuccess;
+}
+
+// Device memory of device `dev` (device or managed allocation), read in place
+// by the kernels. Allocates nothing.
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -81,12 +138,17 @@ extern "C" mpn_status mpn_propagate_noalloc(const uint8_t *mask, int32_t H, int3
     if (ntiles > kNaMaxTiles) return MPN_EINVAL;
 
     cudaStream_t st = (cudaStream_t)stream;
-    unsigned char *base = nullptr;
-    cudaError_t e = scratch_address(&base);
-    if (e != cudaSuccess) return MPN_ECUDA;
     int dev = 0, sms = 0, bps = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return MPN_ECUDA;
+    // the kernels read and write these in place: all three must be memory of
+    // the current device
+    if (!on_device(mask, dev) || !on_device(targets, dev) || !on_device(dist, dev))
+        return MPN_EINVAL;
+    unsigned char *base = nullptr;
+    e = scratch_address(dev, &base);
+    if (e != cudaSuccess) return MPN_ECUDA;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = propagate_blocks_per_sm(kNaVariant, 32, &bps);
     if (e != cudaSuccess || bps < 1) return MPN_ECUDA;
 

@@ -322,11 +322,26 @@ def mpn_launch_count() -> int:
 def mpn_propagate_noalloc(mask, H: int, W: int, targets, dist, max_layers: int = 0,
                           stream=None):
     """Distances into the caller's device buffer `dist` (H*W uint32) with no
-    allocation; mask, targets and dist must be CUDA tensors. Returns the
-    status code (MPN_OK, MPN_EINVAL past 2048 x 2048, ...)."""
-    n = int(targets.numel() if hasattr(targets, "numel") else np.asarray(targets).size)
-    return int(load().mpn_propagate_noalloc(_ptr(mask)[0], H, W, _ptr(targets)[0], n, max_layers,
-                                            _ptr(dist)[0], _stream_handle(stream)))
+    allocation; mask (H*W uint8), targets (32-bit indices) and dist must be
+    CUDA tensors. Returns the status code (MPN_OK, MPN_EINVAL past 2048 x
+    2048, ...). Raises ValueError/TypeError for buffers the kernels cannot
+    use in place (host memory, wrong element size, too few elements)."""
+    for name, a in (("mask", mask), ("targets", targets), ("dist", dist)):
+        if not hasattr(a, "data_ptr") or a.device.type != "cuda":
+            raise TypeError(f"mpn_propagate_noalloc: {name} must be a CUDA tensor")
+        if not a.is_contiguous():
+            raise ValueError(f"mpn_propagate_noalloc: {name} must be contiguous")
+    if H < 1 or W < 1:
+        raise ValueError("mpn_propagate_noalloc: H and W must be >= 1")
+    if mask.element_size() != 1 or mask.numel() < H * W:
+        raise ValueError("mpn_propagate_noalloc: mask must hold H*W bytes")
+    if dist.element_size() != 4 or dist.numel() < H * W:
+        raise ValueError("mpn_propagate_noalloc: dist must hold H*W 32-bit elements")
+    if targets.element_size() != 4:
+        raise ValueError("mpn_propagate_noalloc: targets must be 32-bit indices")
+    n = int(targets.numel())
+    return int(load().mpn_propagate_noalloc(mask.data_ptr(), H, W, targets.data_ptr(), n,
+                                            max_layers, dist.data_ptr(), _stream_handle(stream)))
 
 
 # ---- convenience wrapper -----------------------------------------------

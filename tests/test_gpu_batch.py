@@ -137,3 +137,33 @@ def test_batch_full_size_members_sample():
         b.run(0)
         for tk, w in zip(tks, ws):
             check(b, tk, w)
+
+
+def test_serve_on_the_real_engine_matches_oracle_alone_and_in_the_mix():
+    """The continuous-batching loop (serve) on the real batched engine:
+    Poisson arrivals, rounds of a few sweeps so that requests arriving while
+    others are on the GPU join later rounds, every served path kept. Each
+    response equals the oracle's paths for that grid, i.e. the result of the
+    grid solved alone, whatever else was in flight."""
+    from paper_2004_00540_gb300.serve import Request, serve
+    ws = small_members(20, side_hi=360, base_seed=120)
+    arr = synth.poisson_arrivals(len(ws), 400.0, seed=3)
+    reqs = [Request(w.mask, w.targets, w.starts, w.dist_bits, float(a)) for w, a in zip(ws, arr)]
+    with pkg.Batch(1 << 30) as b:
+        rep = serve(b, reqs, round_sweeps=4, keep_results=True)
+        assert b.stats()["graph"] == 1
+    assert not rep.failed and len(rep.results) == len(ws)
+    assert rep.rounds > 3
+    for i, w in enumerate(ws):
+        od, _ = oracle.bfs(w.mask, w.targets)
+        off, cells, status = oracle.trace(w.mask, od, w.starts)
+        got = rep.results[i]
+        assert np.array_equal(got.offsets, off), w.name
+        assert np.array_equal(got.status, status), w.name
+        assert np.array_equal(got.cells, cells), w.name
+    # one grid served alone gives the same response
+    with pkg.Batch(1 << 28) as b:
+        alone = serve(b, [Request(ws[5].mask, ws[5].targets, ws[5].starts, ws[5].dist_bits, 0.0)],
+                      round_sweeps=4, keep_results=True)
+    assert np.array_equal(alone.results[0].cells, rep.results[5].cells)
+    assert np.array_equal(alone.results[0].offsets, rep.results[5].offsets)

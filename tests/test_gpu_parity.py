@@ -360,6 +360,32 @@ def test_log_fallbacks_stay_exact(chunks, slots, monkeypatch):
             assert np.array_equal(widen(got), d)
 
 
+@pytest.mark.parametrize("hook,value", [("MPN_TEST_SWEEP_CAP", "2"), ("MPN_TEST_SPIN_LIMIT", "1")])
+def test_device_waits_run_out_then_context_recovers(hook, value, monkeypatch):
+    """A device-side limit made to run out on purpose: the sweep cap (2
+    sweeps on a grid that needs hundreds) or the grid barrier's spin limit (a
+    wait of one poll while another block is still in its first visit). The
+    kernel records the error and every block returns -- nothing hangs or
+    faults -- and the call reports MPN_ETIMEOUT. The same context then solves
+    the grid exactly once the hook is gone."""
+    m, t, s = rand_case(2048, 2048, 0.3, 1, 20, 91)
+    d, L = oracle.bfs(m, t)
+    assert L > 200
+    with pkg.Planner(m, pkg.MPN_DIST_U32) as pl:
+        pl.set_tuning(0, 16)
+        monkeypatch.setenv(hook, value)
+        with pytest.raises(pkg.MPNError) as e:
+            pl.propagate(t)
+        assert e.value.status == pkg.MPN_ETIMEOUT
+        monkeypatch.delenv(hook)
+        assert pl.propagate(t) == L
+        assert np.array_equal(widen(pl.distances()), d)
+        paths = pl.trace(s)
+    off, cells, status = oracle.trace(m, d, s)
+    assert np.array_equal(paths.offsets, off) and np.array_equal(paths.status, status)
+    assert np.array_equal(paths.cells, cells)
+
+
 def test_autotune_records_choice_and_stays_exact():
     m, t, s = rand_case(1500, 1400, 0.3, 6, 40, 77)
     with pkg.Planner(m) as pl:

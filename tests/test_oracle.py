@@ -344,3 +344,43 @@ def test_parallel_cpu_baseline_errors():
     with pytest.raises(oracle.OracleError) as e:
         oracle.bfs_parallel(m, np.array([25], np.uint32))
     assert e.value.code == oracle.EINVAL
+
+
+def read_euclid_golden():
+    """Hand-worked Euclidean reconstruction cases (tests/golden/euclid_cases.txt)."""
+    cases, cur = [], None
+    for line in open(os.path.join(GOLD, "euclid_cases.txt")):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "case":
+            cur = {"name": f[1]}
+            cases.append(cur)
+        elif f[0] == "H":
+            cur["H"], cur["W"] = int(f[1]), int(f[3])
+        else:
+            cur[f[0]] = [int(v) for v in f[1:]]
+    for c in cases:
+        m = np.zeros((c["H"], c["W"]), np.uint8)
+        for o in c["obstacles"]:
+            m.reshape(-1)[o] = 1
+        c["mask"] = m
+    return cases
+
+
+def test_euclid_golden_plateau_rules():
+    """Eq. 1's order, the corner-of-diagonal step, the squeeze step and the
+    forward straightening, each pinned by a case worked out by hand."""
+    cases = read_euclid_golden()
+    assert [c["name"] for c in cases] == ["left_before_up", "corner_step", "corner_blocked_left",
+                                          "squeeze"]
+    for c in cases:
+        d, _ = oracle.bfs(c["mask"], c["targets"])
+        off, cells, status = oracle.euclid_trace(c["mask"], d, c["start"])
+        assert status.tolist() == [0], c["name"]
+        assert cells.tolist() == c["path"], c["name"]
+        # the straightened path keeps the raw walk's end-points and order
+        raw = c["raw"]
+        assert raw[0] == c["path"][0] and raw[-1] == c["path"][-1]
+        it = iter(raw)
+        assert all(p in it for p in c["path"]), c["name"]

@@ -270,7 +270,7 @@ mpn_status configure(mpn_ctx *c, int variant, int depth) {
     long long blocks = (long long)bps * c->sm_count;
     if (blocks > ntiles) blocks = ntiles;
     if (blocks < 1) blocks = 1;
-    MPN_TRY(c->tiles.ensure(((size_t)ntiles * (6 + 4 * kTileSlots) + 4) * sizeof(uint32_t)));
+    MPN_TRY(c->tiles.ensure(tile_queue_words((size_t)ntiles, true) * sizeof(uint32_t)));
     c->variant = variant;
     c->depth = depth;
     c->TY = TY;
@@ -537,15 +537,12 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     mpn_status st = begin_propagate(c, targets, n, &dt, log_chunks == 0);
     if (st != MPN_OK) return st;
     const size_t ntiles = (size_t)c->ntx * c->nty;
-    // queue stamps, latest log headers and logged-visit counts of every tile
-    MPN_TRY(cudaMemsetAsync(c->tiles.p, 0, 3 * ntiles * sizeof(uint32_t), c->stream));
     PropParams p{};
     p.g = c->grid();
-    p.queued = (uint32_t *)c->tiles.p;
-    p.tile_head = p.queued + ntiles;
-    p.tile_nv = p.queued + 2 * ntiles;
-    p.lists = p.queued + 3 * ntiles;
-    p.tile_vis = reinterpret_cast<uint4 *>(p.queued + ((6 * ntiles + 3) & ~(size_t)3));   // 16-byte aligned
+    size_t clear_words = 0;
+    layout_tile_queue((uint32_t *)c->tiles.p, ntiles, true, &p, &clear_words);
+    // queue stamps, done stamps, latest log headers, logged-visit counts, lists
+    MPN_TRY(cudaMemsetAsync(c->tiles.p, 0, clear_words * sizeof(uint32_t), c->stream));
     p.ctl = (Ctl *)c->ctl.p;
     p.ntx = c->ntx;
     p.nty = c->nty;
@@ -554,6 +551,9 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     p.TXW = c->TXW;
     p.max_layers = max_layers;
     p.spin_limit = kSpinLimit;
+    p.lookahead = 1;
+    // (test hook: MPN_TEST_NO_LOOKAHEAD=1 makes blocks only wait at a sweep's end)
+    if (const char *e = getenv("MPN_TEST_NO_LOOKAHEAD")) p.lookahead = (e[0] == '1') ? 0u : 1u;
     p.log = log_chunks ? (uint32_t *)c->log.p : nullptr;
     p.log_chunks = log_chunks;
     const uint64_t bound = (max_layers ? (uint64_t)max_layers : (uint64_t)c->H * c->W) / c->depth + 3;

@@ -27,8 +27,8 @@ constexpr uint32_t FB_NW = 32u, FB_NE = 64u, FB_SW = 128u, FB_SE = 256u;
 struct Ctl {
     unsigned int bar_count;        // grid-barrier arrivals of this launch (monotonic)
     unsigned int log_next;         // next free chunk of the activation log
-    unsigned int work[3];          // claim counters of the tile lists, by sweep mod 3
-    unsigned int list_len[3];      // lengths of the tile lists, by sweep mod 3
+    unsigned int work[4];          // claim counters of the tile lists, by sweep mod kListSlots
+    unsigned int list_len[4];      // lengths of the tile lists, by sweep mod kListSlots
     unsigned int err;
     unsigned int max_layer;        // largest activation layer seen
     unsigned int sweeps;
@@ -54,13 +54,29 @@ struct GridDev {
     int H, W, P;
 };
 
+// Tile queue of one propagation. Sweep s takes its tiles from list s mod
+// kListSlots; an entry holds 1 + the tile id (0: not written yet), and the
+// block that takes an entry clears it, so a list slot is all zeros again when
+// it is reused. A tile is queued for sweep s at most once: stamps[s mod
+// kStampSlots][t] = s + 1 once it is (only grows). done[t] = 1 + the last sweep
+// whose visit of t has finished (its writes published). Visits of sweep s
+// queue tiles for s + 1, and a block waiting at the end of sweep s may already
+// run tiles of sweep s + 1 (which queue for s + 2), so three stamp arrays and
+// four list slots keep every sweep's bookkeeping apart.
+constexpr int kStampSlots = 3;
+constexpr int kListSlots = 4;
+// words per tile of the queue buffer before the visit slots: stamps, done,
+// latest log header, logged-visit count, lists
+constexpr int kTileQueueWords = kStampSlots + 1 + 2 + kListSlots;
+
 struct PropParams {
     GridDev g;
-    uint32_t *queued;            // per tile: 1 + last sweep it was queued for
+    uint32_t *stamps;            // kStampSlots arrays of ntiles: 1 + sweep the tile is queued for
+    uint32_t *done;              // per tile: 1 + last sweep whose visit of it finished
     uint32_t *tile_head;         // per tile: 1 + log index of its latest visit header, 0 = none
     uint32_t *tile_nv;           // per tile: visits that logged entries
     uint4 *tile_vis;             // per tile: kTileSlots slots {header index, entry count, l0 + 1, 0} of visit n
-    uint32_t *lists;             // 3 tile lists of ntx * nty entries, by sweep mod 3
+    uint32_t *lists;             // kListSlots tile lists of ntx * nty entries (1 + tile id)
     Ctl *ctl;
     int ntx, nty;                // tiles
     int k;                       // temporal depth (layers per sweep), halo rows
@@ -68,6 +84,7 @@ struct PropParams {
     int TXW;                     // interior words per tile
     uint32_t max_layers;         // 0 = until nothing changes
     uint32_t spin_limit;         // barrier wait limit (iterations of ~100 ns)
+    uint32_t lookahead;          // 1: blocks waiting at a sweep's end run ready tiles of the next
     uint32_t sweep_cap;          // more sweeps than this is an error
     uint32_t *log;               // activation log (log_chunks chunks), or null
     uint32_t log_chunks;
@@ -94,6 +111,30 @@ struct PropParams {
 constexpr uint32_t kLogChunk = 4096;
 constexpr uint32_t kTileSlots = 64;
 constexpr uint32_t kLogFields = 8;
+
+// Words of the tile-queue buffer for ntiles tiles: kTileQueueWords per tile
+// (stamps, done, latest header, logged-visit count, lists), then, 16-byte
+// aligned, kTileSlots visit slots of 4 words per tile when with_slots.
+inline size_t tile_queue_words(size_t ntiles, bool with_slots) {
+    const size_t head = (kTileQueueWords * ntiles + 3) & ~(size_t)3;
+    return head + (with_slots ? 4 * (size_t)kTileSlots * ntiles : 0);
+}
+
+// Point p's queue arrays into buf (tile_queue_words(ntiles, with_slots)
+// words, 16-byte aligned). The first kTileQueueWords * ntiles words must be
+// zero before each propagation (returned in *clear_words).
+inline void layout_tile_queue(uint32_t *buf, size_t ntiles, bool with_slots, PropParams *p,
+                              size_t *clear_words) {
+    p->stamps = buf;
+    p->done = buf + kStampSlots * ntiles;
+    p->tile_head = p->done + ntiles;
+    p->tile_nv = p->tile_head + ntiles;
+    p->lists = p->tile_nv + ntiles;
+    p->tile_vis = with_slots
+                      ? reinterpret_cast<uint4 *>(buf + ((kTileQueueWords * ntiles + 3) & ~(size_t)3))
+                      : nullptr;
+    *clear_words = kTileQueueWords * ntiles;
+}
 
 struct VariantDesc {
     int rxw;      // region words (lanes per row group x words per lane)

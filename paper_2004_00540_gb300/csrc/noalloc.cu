@@ -38,7 +38,7 @@ constexpr int kNaDepth = 32;
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kNaPlaneBytes = align256(kNaPlaneWords * sizeof(uint32_t));
-constexpr size_t kNaTileBytes = align256(kNaMaxTiles * 4 * sizeof(uint32_t));
+constexpr size_t kNaTileBytes = align256((kTileQueueWords * kNaMaxTiles + 3) / 4 * 4 * sizeof(uint32_t));
 constexpr size_t kNaCtlBytes = align256(sizeof(Ctl));
 constexpr size_t kNaScratchBytes = 5 * kNaPlaneBytes + kNaTileBytes + kNaCtlBytes;
 
@@ -159,22 +159,22 @@ extern "C" mpn_status mpn_propagate_noalloc(const uint8_t *mask, int32_t H, int3
     const size_t plane_bytes = (size_t)H * P * sizeof(uint32_t);
 
     // what must start at zero (the array keeps the previous call's contents)
+    PropParams p{};
+    size_t clear_words = 0;
+    layout_tile_queue(tiles, ntiles, false, &p, &clear_words);
     e = cudaMemsetAsync(state, 0, 4 * plane_bytes, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(tiles, 0, ntiles * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(tiles, 0, clear_words * sizeof(uint32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dist, 0xff, (size_t)H * W * sizeof(uint32_t), st);
     if (e == cudaSuccess) e = launch_pack(mask, H, W, P, free_bits, st);
     if (e != cudaSuccess) return MPN_ECUDA;
 
-    PropParams p{};
     p.g.free_bits = free_bits;
     p.g.state = state;
     p.g.dist = dist;
     p.g.H = H;
     p.g.W = W;
     p.g.P = P;
-    p.queued = tiles;
-    p.lists = tiles + ntiles;
     p.ctl = ctl;
     p.ntx = ntx;
     p.nty = nty;
@@ -183,6 +183,7 @@ extern "C" mpn_status mpn_propagate_noalloc(const uint8_t *mask, int32_t H, int3
     p.TXW = TXW;
     p.max_layers = max_layers;
     p.spin_limit = 1u << 24;
+    p.lookahead = 1;
     const uint64_t bound = (max_layers ? (uint64_t)max_layers : (uint64_t)H * W) / kNaDepth + 3;
     p.sweep_cap = (uint32_t)(bound < (1u << 22) ? bound : (1u << 22));
     long long blocks = (long long)bps * sms;

@@ -30,15 +30,25 @@ using wave::ld_relaxed;
 using wave::border_bits;
 
 // Queue tile (ty, tx) for sweep s unless it is queued already (one entry per
-// tile per sweep: the stamp only grows).
+// tile per sweep: the sweep's stamp only grows). The entry holds 1 + the tile
+// id; a block that waits at the end of the previous sweep may poll it.
 __device__ __forceinline__ void push_tile(const PropParams &p, int ty, int tx, uint32_t s) {
     if (ty < 0 || tx < 0 || ty >= p.nty || tx >= p.ntx) return;
     const int t = ty * p.ntx + tx;
-    if (atomicMax(p.queued + t, s + 1) < s + 1) {
-        const uint32_t slot = s % 3;
+    const size_t ntl = (size_t)p.ntx * p.nty;
+    if (atomicMax(p.stamps + (size_t)(s % kStampSlots) * ntl + t, s + 1) < s + 1) {
+        const uint32_t slot = s % kListSlots;
         const uint32_t i = atomicAdd(&p.ctl->list_len[slot], 1u);
-        p.lists[(size_t)slot * p.ntx * p.nty + i] = (uint32_t)t;
+        wave::st_relaxed(p.lists + (size_t)slot * ntl + i, (uint32_t)t + 1u);
     }
+}
+
+// Take entry i of a tile list: the tile id (-1 if the entry was never
+// written), and clear the entry for the list slot's next use.
+__device__ __forceinline__ int take_entry(uint32_t *list, uint32_t i) {
+    const uint32_t e = ld_relaxed(list + i);
+    if (e) wave::st_relaxed(list + i, 0u);
+    return (int)e - 1;
 }
 
 // Queue every tile that frontier cells in these border zones of tile
@@ -72,6 +82,15 @@ __device__ __forceinline__ int zone_tile(const PropParams &p, int ty, int tx, ui
 // visit, and append the tile to the list once the next visit's layers are
 // done, so neither atomic's round trip stands between two visits; the last
 // visit of a sweep finishes its pushes before the grid barrier.
+//
+// Lookahead at the end of a sweep: a block that has arrived at the grid
+// barrier of sweep s does not only wait. It takes entries of sweep s + 1's
+// list (its own first entry, then entries claimed with the counter) and runs
+// a tile as soon as every tile of its 3 x 3 neighbourhood that sweep s still
+// had to visit has finished that visit (stamps and done[] say which): the
+// tile's region then holds exactly the state at the start of sweep s + 1,
+// which is what the visit must read, so the result is the same as after the
+// barrier. Such a visit queues what it reaches for sweep s + 2 at once.
 template <int RXW, int R, int NW, int MINB, typename DT, int WPL = 1>
 __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     static_assert(RXW == 4 || RXW == 8 || RXW == 16 || RXW == 32, "region words");
@@ -82,9 +101,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     __shared__ uint32_t s_len;                              // length of this sweep's list
     __shared__ int s_chunk;                                 // activation-log chunk, -1: none
     __shared__ unsigned s_cursor;                           // entries used in it
+    __shared__ int s_dec[2];   // end of sweep, by poll parity: -3 stop, -2 wait, -1 go on, >= 0 run tile
 
     const int ntiles = p.ntx * p.nty;
     Ctl *ctl = p.ctl;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned thr_maxl = 0u;              // largest layer this thread's words reached
     unsigned long long blk_visits = 0;   // thread 0: tile visits of this block
     unsigned long long blk_layers = 0;   // thread 0: layers those visits ran
@@ -96,6 +117,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     uint32_t prev_nv = 0u;               // thread 0: the tile's logged visits before it
     unsigned long long blk_entries = 0;  // thread 0: word entries this block logged
     const wave::LogSink lg{p.log, &s_chunk, &s_cursor};
+    int pend_mine = -1;                  // thread 0: list index claimed while waiting, not yet run
+    __shared__ int s_done_t;             // visited tile whose done stamp is not out yet (-1: none)
+    __shared__ uint32_t s_done_v;        // its stamp
 
     sm.zero_pad();   // (the first barrier below publishes it)
     // the seeding step rejected the targets (nothing in this kernel sets these
@@ -113,36 +137,99 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     if (threadIdx.x == 0) {
         // sweep 0: entry blockIdx.x of the seeded list is this block's first tile
         s_len = ld_acquire(&ctl->list_len[0]);
-        s_tile = (blockIdx.x < s_len) ? (int)ld_relaxed(p.lists + blockIdx.x) : -1;
+        s_tile = (blockIdx.x < s_len) ? take_entry(p.lists, blockIdx.x) : -1;
         s_chunk = -1;
         s_cursor = 0u;
+        s_done_t = -1;
     }
     __syncthreads();
+
+    // thread 0, before a visit of tile t: room in the log chunk, the header
+    // slot, the tile's chain so far (its previous visit has finished)
+    auto log_begin = [&](int t) {
+        if (log_more && (s_chunk < 0 || s_cursor + maxv > kLogChunk)) {
+            // this chunk may not hold the visit's entries: take the next one
+            const uint32_t c = atomicAdd(&ctl->log_next, 1u);
+            log_more = c < p.log_chunks;
+            s_chunk = log_more ? (int)c : -1;
+            s_cursor = 0u;
+        }
+        if (s_chunk >= 0) {   // the header goes in front of the visit's entries
+            hdr = s_cursor;
+            s_cursor = hdr + 1u;
+            prev_head = ld_relaxed(p.tile_head + t);
+            prev_nv = ld_relaxed(p.tile_nv + t);
+        }
+    };
+    // one thread: publish the done stamp of the last visited tile with a
+    // release store, which orders the visit's writes (state, log, header;
+    // block barriers between) before the stamp: a reader that sees the stamp
+    // sees them.
+    auto publish_done = [&]() {
+        const int dt = s_done_t;
+        if (dt >= 0) {
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p.done + dt), "r"(s_done_v) : "memory");
+            s_done_t = -1;
+        }
+    };
+    // during a visit's layers, thread 32 (nothing of its own in flight then,
+    // so the release costs little) publishes the previous visit's stamp
+    auto hook = [&]() {
+        if (threadIdx.x == 32) publish_done();
+    };
+    // thread 0, after the visit's block barrier: its header (unless it logged
+    // nothing: then the slot is reused); the tile's done stamp is due
+    auto log_end_and_done = [&](int t, uint32_t l0v, uint32_t sweep) {
+        if (s_chunk >= 0) {
+            const uint32_t cnt = s_cursor - hdr - 1u;
+            if (cnt) {
+                const uint32_t gh = (uint32_t)s_chunk * kLogChunk + hdr;
+                uint4 *h = reinterpret_cast<uint4 *>(p.log + (size_t)gh * kLogFields);
+                h[0] = make_uint4(prev_head, cnt, l0v + 1u, prev_nv);
+                h[1] = make_uint4(0u, 0u, 0u, 0u);
+                p.tile_head[t] = gh + 1u;
+                p.tile_nv[t] = prev_nv + 1u;
+                if (prev_nv < kTileSlots)
+                    p.tile_vis[(size_t)t * kTileSlots + prev_nv] = make_uint4(gh, cnt, l0v + 1u, 0u);
+                blk_entries += cnt;
+            } else {
+                s_cursor = hdr;
+            }
+        }
+        s_done_t = t;   // published by the next visit's hook, or before the block waits
+        s_done_v = sweep + 1u;
+    };
+
     for (uint32_t s = 0;; ++s) {
         const uint32_t l0 = s * (uint32_t)p.k;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            // slot (s + 2) % 3 last served sweep s - 1 and next serves s + 2
-            ctl->work[(s + 2) % 3] = 0u;
-            ctl->list_len[(s + 2) % 3] = 0u;
+            // list slot (s + 3) % 4 last served sweep s - 1 (no block claims
+            // from it any more) and next serves sweep s + 3
+            const uint32_t r = (s + 3) % kListSlots;
+            ctl->work[r] = 0u;
+            ctl->list_len[r] = 0u;
         }
         v.l0 = l0;
         v.jmax = p.k;
         if (p.max_layers && l0 + (uint32_t)p.k > p.max_layers) v.jmax = (int)(p.max_layers - l0);
         v.par = (int)(s & 1u);
-        const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
-        unsigned *work = &ctl->work[s % 3];
+        uint32_t *list = p.lists + (size_t)(s % kListSlots) * ntl;
+        unsigned *work = &ctl->work[s % kListSlots];
         const uint32_t len = s_len;
         // entries 0..G-1 go one per block without an atomic; the rest are
-        // claimed with the counter
+        // claimed with the counter (an index claimed while waiting at the last
+        // barrier comes first)
         int t = s_tile;
         if (t < 0 && threadIdx.x == 0) {
-            const uint32_t i = G + atomicAdd(work, 1u);
-            s_tile = (i < len) ? (int)ld_relaxed(list + i) : -1;
+            const uint32_t i = pend_mine >= 0 ? (uint32_t)pend_mine : G + atomicAdd(work, 1u);
+            pend_mine = -1;
+            s_tile = (i < len) ? take_entry(list, i) : -1;
         }
         __syncthreads();
         t = s_tile;
         const uint32_t stamp = s + 2u;             // queued for sweep s + 1
-        const uint32_t slot1 = (s + 1u) % 3u;
+        const uint32_t slot1 = (s + 1u) % kListSlots;
+        uint32_t *stamps1 = p.stamps + (size_t)((s + 1u) % kStampSlots) * ntl;
         int pend_t = -1;                           // lanes 0..8: tile of a push in flight
         uint32_t pend_old = 0u;                    // its stamp before the atomicMax
         while (t >= 0) {
@@ -150,27 +237,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             uint32_t next_i = 0;
             vq ^= 1u;
             if (threadIdx.x == 0) {
-                next_i = G + atomicAdd(work, 1u);
+                if (pend_mine >= 0) {
+                    next_i = (uint32_t)pend_mine;
+                    pend_mine = -1;
+                } else {
+                    next_i = G + atomicAdd(work, 1u);
+                }
                 s_mask[vq] = 0u;   // last read two visits ago, before the previous visit's first barrier
-                if (log_more && (s_chunk < 0 || s_cursor + maxv > kLogChunk)) {
-                    // this chunk may not hold the visit's entries: take the next one
-                    const uint32_t c = atomicAdd(&ctl->log_next, 1u);
-                    log_more = c < p.log_chunks;
-                    s_chunk = log_more ? (int)c : -1;
-                    s_cursor = 0u;
-                }
-                if (s_chunk >= 0) {   // the header goes in front of the visit's entries
-                    hdr = s_cursor;
-                    s_cursor = hdr + 1u;
-                    prev_head = ld_relaxed(p.tile_head + t);   // written before a grid barrier
-                    prev_nv = ld_relaxed(p.tile_nv + t);
-                }
+                log_begin(t);
             }
             v.ty = t / p.ntx;
             v.tx = t - v.ty * p.ntx;
             uint32_t fmask;
             unsigned lastj, jrun = 0;
-            wave::visit_tile<RXW, R, NW, WPL>(v, sm, &ctl->err, &fmask, &lastj, lg, &jrun);
+            wave::visit_tile<RXW, R, NW, WPL>(v, sm, &ctl->err, &fmask, &lastj, lg, &jrun, hook);
             uint32_t pend_i = 0u;
             const bool pend_new = pend_t >= 0 && pend_old < stamp;   // previous visit's push
             if (pend_new) pend_i = atomicAdd(&ctl->list_len[slot1], 1u);
@@ -179,49 +259,157 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             if (threadIdx.x == 0) {
                 ++blk_visits;
                 blk_layers += jrun;
-                s_tile = (next_i < len) ? (int)ld_relaxed(list + next_i) : -1;
+                s_tile = (next_i < len) ? take_entry(list, next_i) : -1;
             }
             __syncthreads();
-            if (threadIdx.x == 0 && s_chunk >= 0) {
-                // the visit's header, unless it logged nothing (then the slot is reused)
-                const uint32_t cnt = s_cursor - hdr - 1u;
-                if (cnt) {
-                    const uint32_t gh = (uint32_t)s_chunk * kLogChunk + hdr;
-                    uint4 *h = reinterpret_cast<uint4 *>(p.log + (size_t)gh * kLogFields);
-                    h[0] = make_uint4(prev_head, cnt, l0 + 1u, prev_nv);
-                    h[1] = make_uint4(0u, 0u, 0u, 0u);
-                    p.tile_head[t] = gh + 1u;
-                    p.tile_nv[t] = prev_nv + 1u;
-                    if (prev_nv < kTileSlots)
-                        p.tile_vis[(size_t)t * kTileSlots + prev_nv] = make_uint4(gh, cnt, l0 + 1u, 0u);
-                    blk_entries += cnt;
-                } else {
-                    s_cursor = hdr;
-                }
-            }
+            if (threadIdx.x == 0) log_end_and_done(t, l0, s);
             if (threadIdx.x < 9) {
-                if (pend_new) p.lists[(size_t)slot1 * ntl + pend_i] = (uint32_t)pend_t;
+                if (pend_new) wave::st_relaxed(p.lists + (size_t)slot1 * ntl + pend_i, (uint32_t)pend_t + 1u);
                 // this visit's push for border zone threadIdx.x: stamp now, append later
                 const uint32_t zone = 1u << threadIdx.x;
                 pend_t = (s_mask[vq] & zone) ? zone_tile(p, v.ty, v.tx, zone) : -1;
-                if (pend_t >= 0) pend_old = atomicMax(p.queued + pend_t, stamp);
+                if (pend_t >= 0) pend_old = atomicMax(stamps1 + pend_t, stamp);
             }
             t = s_tile;
         }
         if (pend_t >= 0 && pend_old < stamp) {   // the sweep's last visit
             const uint32_t i = atomicAdd(&ctl->list_len[slot1], 1u);
-            p.lists[(size_t)slot1 * ntl + i] = (uint32_t)pend_t;
+            wave::st_relaxed(p.lists + (size_t)slot1 * ntl + i, (uint32_t)pend_t + 1u);
         }
 
-        if (!wave::grid_barrier(ctl, (s + 1) * G, p.spin_limit, &s_ok)) return;
+        // ---- end of sweep s: arrive, then run ready tiles of sweep s + 1
+        // until every block has arrived ----
+        const unsigned target = (s + 1) * G;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            publish_done();
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
+        }
+        const uint32_t l1 = l0 + (uint32_t)p.k;          // layer at the start of sweep s + 1
+        const bool more = !(p.max_layers && l1 >= p.max_layers) && s + 1 < p.sweep_cap;
+        const bool look = p.lookahead && more;
+        uint32_t *list1 = p.lists + (size_t)slot1 * ntl;
+        const uint32_t *stamps0 = p.stamps + (size_t)(s % kStampSlots) * ntl;
+        bool fixed_taken = false;                          // thread 0: this block's first entry of s + 1 ran
+        unsigned spins = 0;                                // thread 0: idle polls
+        int toggle = 0;                                    // thread 0: which candidate to check first
+        for (unsigned it = 0;; it ^= 1u) {
+            if (warp == 0) {
+                int dec = -2, cand = -1, cidx = -1;
+                if (lane == 0) {
+                    // the candidate entries, then the barrier word with acquire
+                    // (a candidate read before it is checked again below)
+                    int fe = -1, me = -1;
+                    if (look) {
+                        if (!fixed_taken) fe = (int)ld_relaxed(list1 + blockIdx.x) - 1;
+                        if (pend_mine >= 0 && (uint32_t)pend_mine < ntl)
+                            me = (int)ld_relaxed(list1 + pend_mine) - 1;
+                    }
+                    const uint32_t bc = ld_acquire(&ctl->bar_count);
+                    if (bc >= target) {
+                        dec = -1;
+                    } else if (look) {
+                        // candidates: this block's own first entry, and one claimed entry
+                        if (fe >= 0 && (me < 0 || !toggle)) {
+                            cand = fe;
+                            cidx = (int)blockIdx.x;
+                        } else if (me >= 0) {
+                            cand = me;
+                            cidx = pend_mine;
+                        }
+                        toggle ^= 1;
+                        // hold one claimed entry while the own one is missing or busy
+                        if (pend_mine < 0 && (fixed_taken || fe < 0 || toggle))
+                            pend_mine = (int)(G + atomicAdd(&ctl->work[slot1], 1u));
+                    }
+                }
+                dec = __shfl_sync(0xffffffffu, dec, 0);
+                cand = __shfl_sync(0xffffffffu, cand, 0);
+                if (dec == -2 && cand >= 0) {
+                    // lanes 0..8: has the neighbour that sweep s still had to visit finished it?
+                    bool ok = true;
+                    if (lane < 9) {
+                        const int cy = cand / p.ntx, cx = cand - cy * p.ntx;
+                        const int ny = cy + lane / 3 - 1, nx = cx + lane % 3 - 1;
+                        if (ny >= 0 && nx >= 0 && ny < p.nty && nx < p.ntx) {
+                            const int n = ny * p.ntx + nx;
+                            // (acquire: a finished visit's writes are seen with its stamp)
+                            const uint32_t st = ld_relaxed(stamps0 + n), dn = ld_acquire(p.done + n);
+                            ok = st != s + 1u || dn >= s + 1u;
+                        }
+                    }
+                    if (__all_sync(0xffffffffu, ok)) {
+                        dec = cand;
+                        if (lane == 0) {
+                            wave::st_relaxed(list1 + cidx, 0u);
+                            if (cidx == (int)blockIdx.x && !fixed_taken) fixed_taken = true;
+                            else pend_mine = -1;
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    if (dec == -2) {
+                        ++spins;
+                        if ((spins & 63u) == 0u && (ld_acquire(&ctl->err) & ERR_TIMEOUT)) dec = -3;
+                        if (spins > p.spin_limit) {
+                            atomicOr(&ctl->err, ERR_TIMEOUT);
+                            dec = -3;
+                        }
+                        if (dec == -2 && spins > 8) __nanosleep(32);
+                    }
+                    s_dec[it] = dec;   // (read two polls ago, before the last block barrier)
+                }
+            }
+            __syncthreads();
+            const int d = s_dec[it];
+            if (d == -3) return;      // a wait ran out (recorded): every block stops
+            if (d == -1) break;       // every block has arrived
+            if (d == -2) continue;
+            // ---- a visit of tile d in sweep s + 1 ----
+            vq ^= 1u;
+            if (threadIdx.x == 0) {
+                s_mask[vq] = 0u;
+                log_begin(d);
+            }
+            wave::Visit v1 = v;
+            v1.l0 = l1;
+            v1.jmax = p.k;
+            if (p.max_layers && l1 + (uint32_t)p.k > p.max_layers) v1.jmax = (int)(p.max_layers - l1);
+            v1.par = (int)((s + 1u) & 1u);
+            v1.ty = d / p.ntx;
+            v1.tx = d - v1.ty * p.ntx;
+            uint32_t fmask;
+            unsigned lastj, jrun = 0;
+            wave::visit_tile<RXW, R, NW, WPL>(v1, sm, &ctl->err, &fmask, &lastj, lg, &jrun);
+            if (fmask) atomicOr(&s_mask[vq], fmask);
+            if (lastj) thr_maxl = max(thr_maxl, l1 + lastj);
+            if (threadIdx.x == 0) {
+                ++blk_visits;
+                blk_layers += jrun;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                log_end_and_done(d, l1, s + 1u);
+                publish_done();   // the block waits anyway: out at once
+                spins = 0;
+            }
+            if (threadIdx.x < 9) {   // what it reaches goes to sweep s + 2 at once
+                const uint32_t zone = 1u << threadIdx.x;
+                if (s_mask[vq] & zone) {
+                    const int nt = zone_tile(p, v1.ty, v1.tx, zone);
+                    if (nt >= 0) push_tile(p, nt / p.ntx, nt - (nt / p.ntx) * p.ntx, s + 2u);
+                }
+            }
+        }
+
         if (threadIdx.x == 0) {
             // decided from values no block changes before the next barrier, so
             // every block reaches the same decision; the same read gives the
-            // next sweep's list length, and this block's first entry of it is
-            // loaded alongside
-            const uint32_t nlen = ld_acquire(&ctl->list_len[(s + 1) % 3]);
-            const int first = (int)ld_relaxed(p.lists + (size_t)((s + 1) % 3) * ntl + blockIdx.x);
-            unsigned done = (nlen == 0u) || (p.max_layers && l0 + (uint32_t)p.k >= p.max_layers);
+            // next sweep's list length
+            // (the barrier's completion was read with acquire; these two loads go out together)
+            const uint32_t nlen = ld_relaxed(&ctl->list_len[slot1]);
+            const uint32_t fe = fixed_taken ? 0u : ld_relaxed(list1 + blockIdx.x);
+            unsigned done = (nlen == 0u) || (p.max_layers && l1 >= p.max_layers);
             if (!done && s + 1 >= p.sweep_cap) {
                 atomicOr(&ctl->err, ERR_SWEEPS);
                 done = 1;
@@ -234,7 +422,19 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             s_done = done;
             s_maxl = 0u;
             s_len = nlen;
-            s_tile = (blockIdx.x < nlen) ? first : -1;
+            // this block's first tile of sweep s + 1: its own entry (unless it
+            // ran already), else the entry it claimed while waiting
+            int first = -1;
+            if (!fixed_taken && blockIdx.x < nlen && fe) {
+                first = (int)fe - 1;
+                wave::st_relaxed(list1 + blockIdx.x, 0u);
+            }
+            if (first < 0 && pend_mine >= 0) {
+                if ((uint32_t)pend_mine < nlen) first = take_entry(list1, (uint32_t)pend_mine);
+                pend_mine = -1;
+            }
+            if (pend_mine >= 0 && (uint32_t)pend_mine >= nlen) pend_mine = -1;   // never written
+            s_tile = first;
         }
         __syncthreads();
         if (s_done) {
@@ -549,7 +749,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
     const uint32_t G = gridDim.x;
     if (threadIdx.x == 0) {
         s_len = ld_acquire(&ctl->list_len[0]);
-        s_first = (blockIdx.x < s_len) ? (int)ld_relaxed(p.lists + blockIdx.x) : -1;
+        s_first = (blockIdx.x < s_len) ? take_entry(p.lists, blockIdx.x) : -1;
     }
     __syncthreads();
     if (ld_acquire(&ctl->err) & (ERR_INVAL | ERR_OBSTACLE)) return;
@@ -564,15 +764,15 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
     for (uint32_t s = 0;; ++s) {
         const uint32_t l0 = s * (uint32_t)p.k;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            ctl->work[(s + 2) % 3] = 0u;
-            ctl->list_len[(s + 2) % 3] = 0u;
+            ctl->work[(s + 3) % kListSlots] = 0u;
+            ctl->list_len[(s + 3) % kListSlots] = 0u;
         }
         v.l0 = l0;
         v.jmax = p.k;
         if (p.max_layers && l0 + (uint32_t)p.k > p.max_layers) v.jmax = (int)(p.max_layers - l0);
         v.par = (int)(s & 1u);
-        const uint32_t *list = p.lists + (size_t)(s % 3) * ntl;
-        unsigned *work = &ctl->work[s % 3];
+        uint32_t *list = p.lists + (size_t)(s % kListSlots) * ntl;
+        unsigned *work = &ctl->work[s % kListSlots];
         const uint32_t len = s_len;
         const int first = s_first;
 
@@ -594,7 +794,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
                 };
                 auto claim = [&]() -> int {
                     const uint32_t i = G + atomicAdd(work, 1u);
-                    return (i < len) ? (int)ld_relaxed(list + i) : -1;
+                    return (i < len) ? take_entry(list, i) : -1;
                 };
                 bool ok = true;
                 int t = first >= 0 ? first : claim();
@@ -670,8 +870,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
 
         if (!wave::grid_barrier(ctl, (s + 1) * G, p.spin_limit, &s_ok)) return;
         if (threadIdx.x == 0) {
-            const uint32_t nlen = ld_acquire(&ctl->list_len[(s + 1) % 3]);
-            const int f = (int)ld_relaxed(p.lists + (size_t)((s + 1) % 3) * ntl + blockIdx.x);
+            const uint32_t nlen = ld_acquire(&ctl->list_len[(s + 1) % kListSlots]);
+            const int f = (blockIdx.x < nlen)
+                              ? take_entry(p.lists + (size_t)((s + 1) % kListSlots) * ntl, blockIdx.x)
+                              : -1;
             unsigned d = (nlen == 0u) || (p.max_layers && l0 + (uint32_t)p.k >= p.max_layers);
             if (!d && s + 1 >= p.sweep_cap) {
                 atomicOr(&ctl->err, ERR_SWEEPS);

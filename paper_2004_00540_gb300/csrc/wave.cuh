@@ -146,6 +146,13 @@ __device__ __forceinline__ void bar_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(NBAR) : "memory");
 }
 
+// A callback that visit_core runs once, on every thread, a few layers into
+// the visit (after the first four layers, or at the end of a shorter visit):
+// a point at which the block's earlier memory operations have completed.
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
 // One tile visit's inputs.
 struct Visit {
     GridDev g;            // planes of the grid the tile belongs to
@@ -226,12 +233,12 @@ __device__ __forceinline__ void hdil2(uint32_t a, uint32_t b, uint32_t &ha, uint
 // row, in registers; slot s = i * WPL + u is word u of row i). Region =
 // (NW * 32 / (RXW / WPL) * R) rows x RXW words; interior = rows [k, RY - k)
 // x words [1, RXW - 1).
-template <int RXW, int R, int NW, bool NAMED, int WPL = 1>
+template <int RXW, int R, int NW, bool NAMED, int WPL = 1, typename Hook = NoHook>
 __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WPL> &sm, uint32_t *err,
                                            uint32_t (&V)[R * WPL], const uint32_t (&F)[R * WPL],
                                            const uint32_t (&OWN)[R * WPL], uint32_t *fmask_out,
                                            unsigned *lastj_out, const LogSink &lg = LogSink(),
-                                           unsigned *jrun_out = nullptr) {
+                                           unsigned *jrun_out = nullptr, const Hook &hook = Hook()) {
     static_assert(WPL == 1 || WPL == 2, "words per lane");
     constexpr int LG = RXW / WPL;   // lanes per row group
     constexpr int GPW = 32 / LG;
@@ -322,7 +329,12 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WP
     // unreached cells: gray(j - 1) -> gray(j), plane ctz(j)
 #define MPN_FLIP(B) _Pragma("unroll") for (int s = 0; s < S; ++s) P[B][s] ^= ~V[s]
     int jdone = v.jmax;   // layers run (fewer when the region turns stable)
+    bool hooked = false;
     for (int j = 1; j <= v.jmax; j += 4) {   // j = 1 mod 4
+        if (j == 5) {
+            hook();
+            hooked = true;
+        }
         if (!layer(sm.xtop[1], sm.xbot[1], Check())) {
             jdone = j - 1;
             break;
@@ -344,6 +356,7 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WP
         }
     }
 #undef MPN_FLIP
+    if (!hooked) hook();
     if (jrun_out) *jrun_out = (unsigned)jdone;
 
     // cells of this tile's interior first reached in this visit
@@ -472,11 +485,11 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WP
 // (A word last changed two or more sweeps back may still carry that sweep's
 // bits in Npar; those cells' whole neighbourhoods were reached by then, so
 // hiding them changes nothing inside the tile.)
-template <int RXW, int R, int NW, int WPL = 1>
+template <int RXW, int R, int NW, int WPL = 1, typename Hook = NoHook>
 __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW, WPL> &sm, uint32_t *err,
                                            uint32_t *fmask_out, unsigned *lastj_out,
                                            const LogSink &lg = LogSink(),
-                                           unsigned *jrun_out = nullptr) {
+                                           unsigned *jrun_out = nullptr, const Hook &hook = Hook()) {
     constexpr int LG = RXW / WPL;
     constexpr int S = R * WPL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -500,7 +513,7 @@ __device__ __forceinline__ void visit_tile(const Visit &v, VisitSmem<RXW, NW, WP
         const uint64_t vn = in ? ld_pair(gd.state + 4 * off + 2 * v.par) : 0ull;
         V[s] = (uint32_t)vn & (own ? 0xffffffffu : ~(uint32_t)(vn >> 32));
     }
-    visit_core<RXW, R, NW, false, WPL>(v, sm, err, V, F, OWN, fmask_out, lastj_out, lg, jrun_out);
+    visit_core<RXW, R, NW, false, WPL>(v, sm, err, V, F, OWN, fmask_out, lastj_out, lg, jrun_out, hook);
 }
 
 }  // namespace wave

@@ -406,13 +406,13 @@ struct mpn_batch {
     uint64_t next_ticket = 1;
     uint32_t next_sweep = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // side streams for the per-grid path walks of a finished round: a walk is
-    // as long as the grid's longest path, so the grids' walks run side by
-    // side instead of one after another on the batch stream
-    static constexpr int kSide = 16;
-    cudaStream_t side[kSide] = {};
-    cudaEvent_t side_ev[kSide] = {};
-    cudaEvent_t fork_ev = nullptr;
+    // the paths of the grids a round finished are measured and walked
+    // together: a job per grid, the walks' lengths and order (grown on demand,
+    // outside the arena budget)
+    WalkJob *d_wjobs = nullptr, *h_wjobs = nullptr;
+    uint64_t *d_totals = nullptr, *h_totals = nullptr;
+    uint32_t *d_walk_len = nullptr, *d_order = nullptr;
+    size_t walk_cap = 0;
     std::map<uint32_t, cudaGraphExec_t> graphs;   // one captured round per max_sweeps value
     bool use_graph = true;
     float last_round_ms = 0.f;
@@ -511,11 +511,10 @@ mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bc, 0, sizeof(BatchCtl), b->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
-    for (int i = 0; i < mpn_batch::kSide && e == cudaSuccess; ++i) {
-        e = cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->side_ev[i], cudaEventDisableTiming);
-    }
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_wjobs, b->max_slots * sizeof(WalkJob));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_wjobs, b->max_slots * sizeof(WalkJob));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_totals, b->max_slots * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_totals, b->max_slots * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         mpn_batch_destroy(b);
@@ -699,23 +698,6 @@ static cudaError_t run_round(mpn_batch *b, const BatchParams &p) {
     return cudaGraphLaunch(it->second, b->stream);
 }
 
-// Side stream i waits for the work queued on the batch stream so far.
-static cudaError_t fork_side(mpn_batch *b) {
-    cudaError_t e = cudaEventRecord(b->fork_ev, b->stream);
-    for (int i = 0; i < mpn_batch::kSide && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(b->side[i], b->fork_ev, 0);
-    return e;
-}
-
-// The batch stream waits for everything queued on the side streams.
-static cudaError_t join_side(mpn_batch *b) {
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < mpn_batch::kSide && e == cudaSuccess; ++i) {
-        e = cudaEventRecord(b->side_ev[i], b->side[i]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->side_ev[i], 0);
-    }
-    return e;
-}
-
 static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t *cells,
                                       cudaStream_t st) {
     char *res = (char *)arena_at(b, m.res_off);
@@ -759,63 +741,74 @@ static mpn_status finish_round(mpn_batch *b) {
             done.push_back(&m);
         }
     }
-    // path lengths and offsets of every newly converged grid, then one wait
+    if (done.empty()) return MPN_OK;
+    // one walk job per newly converged grid: status, lengths, offsets and
+    // totals of all of them in one launch, then one wait
     Ctl *ctl = &b->d_bc->c;
-    if (!done.empty()) {
-        B_TRY(fork_side(b));
-        int j = 0;
-        for (HostMaze *m : done) {
-            cudaStream_t ss = b->side[j++ % mpn_batch::kSide];
-            char *res = (char *)arena_at(b, m->res_off);
-            GridDev g;
-            g.free_bits = (const uint32_t *)arena_at(b, m->planes_off);
-            g.state = nullptr;
-            g.dist = res + m->dist_o;
-            g.H = m->H;
-            g.W = m->W;
-            g.P = m->P;
-            B_TRY(cudaMemsetAsync(res + m->off_o, 0, 8, ss));
-            if (m->ns > 0) {
-                B_TRY(launch_trace_lengths(g, m->dist_bits, (const uint32_t *)(res + m->st_o), m->ns,
-                                           (uint64_t *)(res + m->off_o), (int8_t *)(res + m->sts_o),
-                                           ctl, ss));
-                B_TRY(launch_scan((uint64_t *)(res + m->off_o), m->ns, ss));
-            }
-        }
-        B_TRY(join_side(b));
-        std::vector<uint64_t> totals(done.size());
-        for (size_t i = 0; i < done.size(); ++i) {
-            char *res = (char *)arena_at(b, done[i]->res_off);
-            B_TRY(cudaMemcpyAsync(&totals[i], (uint64_t *)(res + done[i]->off_o) + done[i]->ns, 8,
-                                  cudaMemcpyDeviceToHost, st));
-        }
-        B_TRY(cudaStreamSynchronize(st));
-        // the bit planes are not needed any more (tracing reads the distances)
-        for (size_t i = 0; i < done.size(); ++i) {
-            done[i]->total = totals[i];
-            done[i]->state = MState::Traced;
-            release_planes(b, *done[i]);
-        }
+    const int nj = (int)done.size();
+    uint64_t nwalks = 0;
+    for (HostMaze *m : done) nwalks += (uint64_t)m->ns;
+    if (nwalks >= 0xffffffffull) return MPN_EINVAL;
+    if (nwalks > b->walk_cap) {
+        size_t cap = b->walk_cap ? b->walk_cap : (1u << 16);
+        while (cap < nwalks) cap *= 2;
+        cudaFree(b->d_walk_len);
+        cudaFree(b->d_order);
+        b->d_walk_len = b->d_order = nullptr;
+        b->walk_cap = 0;
+        B_TRY(cudaMalloc((void **)&b->d_walk_len, cap * sizeof(uint32_t)));
+        B_TRY(cudaMalloc((void **)&b->d_order, cap * sizeof(uint32_t)));
+        b->walk_cap = cap;
     }
-    // paths of every finished grid whose paths fit in the arena now; the
-    // others are traced on demand into the caller's buffer
-    bool launched = false;
-    if (!done.empty()) B_TRY(fork_side(b));
-    int j = 0;
-    for (HostMaze *m : done) {
+    uint32_t base = 0;
+    for (int j = 0; j < nj; ++j) {
+        const HostMaze *m = done[j];
+        char *res = (char *)arena_at(b, m->res_off);
+        WalkJob &jb = b->h_wjobs[j];
+        jb.g.free_bits = (const uint32_t *)arena_at(b, m->planes_off);
+        jb.g.state = nullptr;
+        jb.g.dist = res + m->dist_o;
+        jb.g.H = m->H;
+        jb.g.W = m->W;
+        jb.g.P = m->P;
+        jb.starts = (const uint32_t *)(res + m->st_o);
+        jb.offsets = (uint64_t *)(res + m->off_o);
+        jb.status = (int8_t *)(res + m->sts_o);
+        jb.cells = nullptr;
+        jb.dist_bits = m->dist_bits;
+        jb.ns = (uint32_t)m->ns;
+        jb.walk_base = base;
+        jb.pad = 0;
+        base += (uint32_t)m->ns;
+    }
+    B_TRY(cudaMemcpyAsync(b->d_wjobs, b->h_wjobs, nj * sizeof(WalkJob), cudaMemcpyHostToDevice, st));
+    B_TRY(launch_batch_lengths(b->d_wjobs, nj, b->d_walk_len, b->d_totals, &ctl->err, st));
+    B_TRY(cudaMemcpyAsync(b->h_totals, b->d_totals, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    B_TRY(cudaStreamSynchronize(st));
+    // the bit planes are not needed any more (walks read the distances);
+    // paths of every finished grid whose paths fit in the arena now, walked
+    // together, longest first; the others are traced on demand into the
+    // caller's buffer
+    bool any = false;
+    for (int j = 0; j < nj; ++j) {
+        HostMaze *m = done[j];
+        m->total = b->h_totals[j];
+        m->state = MState::Traced;
+        release_planes(b, *m);
         m->cells_bytes = align_up((size_t)(m->total ? m->total : 1) * 4);
         if (!b->mem.alloc(m->cells_bytes, &m->cells_off)) {
             m->cells_bytes = 0;
             continue;
         }
-        if (m->ns > 0)
-            B_TRY(launch_batch_trace(b, *m, (uint32_t *)arena_at(b, m->cells_off),
-                                     b->side[j++ % mpn_batch::kSide]));
+        b->h_wjobs[j].cells = (uint32_t *)arena_at(b, m->cells_off);
         m->paths_ready = true;
-        launched = true;
+        any = any || m->total > 0;
     }
-    if (!done.empty()) B_TRY(join_side(b));
-    if (launched) B_TRY(cudaStreamSynchronize(st));
+    if (any) {
+        B_TRY(cudaMemcpyAsync(b->d_wjobs, b->h_wjobs, nj * sizeof(WalkJob), cudaMemcpyHostToDevice, st));
+        B_TRY(launch_batch_walks(b->d_wjobs, nj, b->d_walk_len, (uint32_t)nwalks, b->d_order, &ctl->err, st));
+        B_TRY(cudaStreamSynchronize(st));
+    }
     return MPN_OK;
 }
 
@@ -1042,14 +1035,12 @@ void mpn_batch_destroy(mpn_batch *b) {
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
-    for (int i = 0; i < mpn_batch::kSide; ++i) {
-        if (b->side[i]) {
-            cudaStreamSynchronize(b->side[i]);
-            cudaStreamDestroy(b->side[i]);
-        }
-        if (b->side_ev[i]) cudaEventDestroy(b->side_ev[i]);
-    }
-    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    cudaFree(b->d_wjobs);
+    cudaFree(b->d_totals);
+    cudaFree(b->d_walk_len);
+    cudaFree(b->d_order);
+    if (b->h_wjobs) cudaFreeHost(b->h_wjobs);
+    if (b->h_totals) cudaFreeHost(b->h_totals);
     delete b;
 }
 

@@ -198,6 +198,30 @@ cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts
                          uint32_t *order, cudaStream_t st, uint32_t *err);
 cudaError_t launch_activity(const GridDev &g, int dist_bits, uint32_t L, int32_t *out,
                             cudaStream_t st);
+
+// One grid of a batched trace: the paths of many grids are measured, ordered
+// and walked together (a walk takes as long as its path, so the grids' walks
+// run side by side in one launch, longest first across all of them).
+struct WalkJob {
+    GridDev g;                  // free_bits (for the start status), dist, H, W, P
+    const uint32_t *starts;     // ns start cells
+    uint64_t *offsets;          // ns + 1: path offsets (written by the lengths step)
+    int8_t *status;             // ns: per-start status
+    uint32_t *cells;            // path cells, or null: the walks of this grid are skipped
+    int dist_bits;
+    uint32_t ns;
+    uint32_t walk_base;         // index of this grid's first walk among all walks of the batch
+    uint32_t pad;
+};
+// Per job: status and path length of every start, offsets (scan), the job's
+// path-cell total in totals[j], and every walk's length (saturated to 32
+// bits) in walk_len[walk_base + i].
+cudaError_t launch_batch_lengths(const WalkJob *jobs, int njobs, uint32_t *walk_len,
+                                 uint64_t *totals, uint32_t *err, cudaStream_t st);
+// The walks of every job with cells, longest first (order: nwalks words of
+// scratch).
+cudaError_t launch_batch_walks(const WalkJob *jobs, int njobs, const uint32_t *walk_len,
+                               uint32_t nwalks, uint32_t *order, uint32_t *err, cudaStream_t st);
 cudaError_t launch_nearest(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
                            const int8_t *status, uint32_t *ends, uint32_t *ends_d, cudaStream_t st,
                            uint32_t *err);

@@ -100,7 +100,7 @@ __global__ void k_lengths(GridDev g, const uint32_t *__restrict__ starts, int n,
 // In-place inclusive scan of a[1..n] by one block: chunks of blockDim * 8
 // elements, each thread summing 8 consecutive values, a warp-shuffle scan over
 // thread sums, and a running carry across chunks.
-__global__ void k_scan(uint64_t *a, int n) {
+__device__ __forceinline__ void block_scan_inplace(uint64_t *a, int n) {
     constexpr int ITEMS = 8;
     __shared__ uint64_t warp_tot[32];
     __shared__ uint64_t carry_s;
@@ -149,32 +149,20 @@ __global__ void k_scan(uint64_t *a, int n) {
     }
 }
 
-// CELLS: write the whole path at offsets[i]; otherwise write only the cell
-// the walk ends at (the target reached) to ends[i] and the start's distance
-// to ends_d[i] (0xFFFFFFFF for both when the start has no path).
-template <typename DT, bool CELLS>
-__global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
-    k_trace(GridDev g, const uint32_t *__restrict__ starts, int n,
-            const uint64_t *__restrict__ offsets, const int8_t *__restrict__ status,
-            uint32_t *__restrict__ cells, uint32_t *__restrict__ ends, uint32_t *__restrict__ ends_d,
-            uint32_t *err, const uint32_t *__restrict__ order) {
-    constexpr int kW = TraceWin<DT>::side, kP = kW + 1, NWp = TraceWin<DT>::warps;
-    __shared__ DT win[NWp][kW * kP];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int slot = blockIdx.x * NWp + wl;
-    if (slot >= n) return;                      // whole warp leaves together
-    const int i = order ? (int)order[slot] : slot;
-    if (i < 0 || i >= n) return;
-    if (status[i] != MPN_PATH_OK) {
-        if (!CELLS && lane == 0) {
-            ends[i] = 0xffffffffu;
-            if (ends_d) ends_d[i] = 0xffffffffu;
-        }
-        return;
-    }
+__global__ void k_scan(uint64_t *a, int n) { block_scan_inplace(a, n); }
+
+// One walk by the calling warp (all 32 lanes), from start c (free, reached)
+// down to a target. wb: the warp's window buffer, kW x (kW + 1) elements of
+// DT. CELLS: the path's cells go to cells[o0], cells[o0 + 1], ...; *end gets
+// the linear index of the cell the walk ends at. False if the plane is not a
+// distance plane (no neighbour one step closer; ERR_TRACE recorded).
+template <typename DT, int kW, bool CELLS>
+__device__ __forceinline__ bool walk_path(const GridDev &g, uint32_t c, uint64_t o0, DT *wb,
+                                          uint32_t *__restrict__ cells, uint32_t *err, uint32_t *end) {
+    constexpr int kP = kW + 1;
+    const int lane = threadIdx.x & 31;
     const DT *dist = reinterpret_cast<const DT *>(g.dist);
     const DT INF = (DT)~(DT)0;
-    DT *wb = win[wl];
     // neighbour of lane q (q < 8) in the tie-break order
     const int my_dy = (lane < 3) ? -1 : (lane < 5 ? 0 : 1);
     const int my_dx = (lane == 0 || lane == 3 || lane == 5) ? -1 : ((lane == 1 || lane == 6) ? 0 : 1);
@@ -189,11 +177,9 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
     const int off2a = off1 + dy2a * kP + dx2a, off2b = off1 + dy2b * kP + dx2b;
     const int my_off = my_dy * kP + my_dx;
 
-    uint32_t c = starts[i];
-    uint64_t o = CELLS ? offsets[i] : 0ull;
+    uint64_t o = o0;
     int cy = (int)(c / (uint32_t)g.W), cx = (int)(c % (uint32_t)g.W);
     uint32_t d = (uint32_t)dist[c];
-    const uint32_t d0 = d;
     if (CELLS && lane == 0) cells[o] = c;
     int ddy = 0, ddx = 0;   // how far the walk moved in the last window
     while (d > 0) {
@@ -245,13 +231,13 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
                 const unsigned mb = __ballot_sync(0xffffffffu, a && b1);
                 if (!m1) {                      // not a distance plane: give up on this path
                     if (lane == 0) atomicOr(err, ERR_TRACE);
-                    return;
+                    return false;
                 }
                 const int g1 = (__ffs(m1) - 1) & ~3;   // 4 * q1
                 const unsigned m2 = ((ma >> g1) & 0xfu) | (((mb >> g1) & 0xfu) << 4);
                 if (!m2) {
                     if (lane == 0) atomicOr(err, ERR_TRACE);
-                    return;
+                    return false;
                 }
                 const int q1 = g1 >> 2, q2 = __ffs(m2) - 1;
                 const int ly1 = ly + (int)((0xa940u >> (2 * q1)) & 3u) - 1;
@@ -271,7 +257,7 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
             const unsigned m = __ballot_sync(0xffffffffu, hit);
             if (!m) {                      // not a distance plane: give up on this path
                 if (lane == 0) atomicOr(err, ERR_TRACE);
-                return;
+                return false;
             }
             // neighbour q's offsets from two packed tables (2 bits per q:
             // offset + 1), the same order as my_dy / my_dx
@@ -288,10 +274,126 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
         cy = wy0 + ly;
         cx = wx0 + lx;
     }
+    *end = (uint32_t)cy * (uint32_t)g.W + (uint32_t)cx;
+    return true;
+}
+
+// CELLS: write the whole path at offsets[i]; otherwise write only the cell
+// the walk ends at (the target reached) to ends[i] and the start's distance
+// to ends_d[i] (0xFFFFFFFF for both when the start has no path).
+template <typename DT, bool CELLS>
+__global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
+    k_trace(GridDev g, const uint32_t *__restrict__ starts, int n,
+            const uint64_t *__restrict__ offsets, const int8_t *__restrict__ status,
+            uint32_t *__restrict__ cells, uint32_t *__restrict__ ends, uint32_t *__restrict__ ends_d,
+            uint32_t *err, const uint32_t *__restrict__ order) {
+    constexpr int kW = TraceWin<DT>::side, kP = kW + 1, NWp = TraceWin<DT>::warps;
+    __shared__ DT win[NWp][kW * kP];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int slot = blockIdx.x * NWp + wl;
+    if (slot >= n) return;                      // whole warp leaves together
+    const int i = order ? (int)order[slot] : slot;
+    if (i < 0 || i >= n) return;
+    if (status[i] != MPN_PATH_OK) {
+        if (!CELLS && lane == 0) {
+            ends[i] = 0xffffffffu;
+            if (ends_d) ends_d[i] = 0xffffffffu;
+        }
+        return;
+    }
+    const uint32_t c = starts[i];
+    const uint32_t d0 = (uint32_t)reinterpret_cast<const DT *>(g.dist)[c];
+    uint32_t e = 0;
+    if (!walk_path<DT, kW, CELLS>(g, c, CELLS ? offsets[i] : 0ull, win[wl], cells, err, &e)) return;
     if (!CELLS && lane == 0) {
-        ends[i] = (uint32_t)cy * (uint32_t)g.W + (uint32_t)cx;
+        ends[i] = e;
         if (ends_d) ends_d[i] = d0;
     }
+}
+
+// ---- batched trace over the grids of a batch ----
+
+// One block per job: the status and length of every start (as k_lengths),
+// the offsets scanned in place, the job's total, and the flat walk lengths.
+__global__ void __launch_bounds__(256) k_lengths_batch(const WalkJob *__restrict__ jobs,
+                                                       uint32_t *__restrict__ walk_len,
+                                                       uint64_t *__restrict__ totals, uint32_t *err) {
+    const WalkJob jb = jobs[blockIdx.x];
+    const GridDev &g = jb.g;
+    const uint64_t N = (uint64_t)g.H * (uint64_t)g.W;
+    if (threadIdx.x == 0) jb.offsets[0] = 0ull;
+    for (uint32_t i = threadIdx.x; i < jb.ns; i += blockDim.x) {
+        const uint32_t s = jb.starts[i];
+        uint64_t len = 0;
+        int8_t stt = MPN_PATH_OK;
+        if ((uint64_t)s >= N) {
+            atomicOr(err, ERR_INVAL);
+            stt = MPN_PATH_UNREACHABLE;
+        } else {
+            const int y = (int)(s / (uint32_t)g.W), x = (int)(s % (uint32_t)g.W);
+            const uint32_t d = jb.dist_bits == 16 ? (uint32_t)reinterpret_cast<const uint16_t *>(g.dist)[s]
+                                                  : reinterpret_cast<const uint32_t *>(g.dist)[s];
+            const uint32_t inf = jb.dist_bits == 16 ? 0xffffu : 0xffffffffu;
+            if (!((g.free_bits[(size_t)y * g.P + (x >> 5)] >> (x & 31)) & 1u)) stt = MPN_PATH_ON_OBSTACLE;
+            else if (d == inf) stt = MPN_PATH_UNREACHABLE;
+            else len = (uint64_t)d + 1u;
+        }
+        jb.offsets[i + 1] = len;
+        jb.status[i] = stt;
+        walk_len[jb.walk_base + i] = len > 0xffffffffull ? 0xffffffffu : (uint32_t)len;
+    }
+    __syncthreads();
+    block_scan_inplace(jb.offsets, (int)jb.ns);
+    if (threadIdx.x == 0) totals[blockIdx.x] = jb.offsets[jb.ns];
+}
+
+// Walk order over flat lengths, longest first (as k_order).
+__global__ void __launch_bounds__(1024) k_order_len(const uint32_t *__restrict__ len, uint32_t n,
+                                                    uint32_t *__restrict__ order) {
+    __shared__ unsigned cnt[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[__clz(len[i])], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned a = 0u;
+        for (int k = 0; k < 33; ++k) {
+            const unsigned c = cnt[k];
+            cnt[k] = a;
+            a += c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) order[atomicAdd(&cnt[__clz(len[i])], 1u)] = i;
+}
+
+// Warp per walk over every job: the walk's job is the last one whose first
+// walk index is not above it (jobs are in walk order). uint32 planes walk 64 x
+// 64 windows, uint16 planes 32 x 32 ones in the same buffer.
+constexpr int kBatchTraceWarps = 2;
+__global__ void __launch_bounds__(kBatchTraceWarps * 32)
+    k_trace_batch(const WalkJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ order,
+                  uint32_t nwalks, uint32_t *err) {
+    __shared__ __align__(16) uint32_t win[kBatchTraceWarps][64 * 65];
+    const int wl = threadIdx.x >> 5;
+    const uint32_t slot = blockIdx.x * kBatchTraceWarps + wl;
+    if (slot >= nwalks) return;                 // whole warp leaves together
+    const uint32_t w = order[slot];
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].walk_base <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    const WalkJob &jb = jobs[lo];
+    const uint32_t i = w - jb.walk_base;
+    if (i >= jb.ns || !jb.cells || jb.status[i] != MPN_PATH_OK) return;
+    uint32_t e = 0;
+    if (jb.dist_bits == 16)
+        walk_path<uint16_t, 32, true>(jb.g, jb.starts[i], jb.offsets[i],
+                                      reinterpret_cast<uint16_t *>(win[wl]), jb.cells, err, &e);
+    else
+        walk_path<uint32_t, 64, true>(jb.g, jb.starts[i], jb.offsets[i], win[wl], jb.cells, err, &e);
 }
 
 // Euclidean path reconstruction (Eq. 1 and the straightening rule after it),
@@ -512,6 +614,31 @@ cudaError_t launch_activity(const GridDev &g, int dist_bits, uint32_t L, int32_t
     count_launch();
     if (dist_bits == 16) k_activity<uint16_t><<<grid_for(n, 256), 256, 0, st>>>(g, L, out);
     else k_activity<uint32_t><<<grid_for(n, 256), 256, 0, st>>>(g, L, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_lengths(const WalkJob *jobs, int njobs, uint32_t *walk_len,
+                                 uint64_t *totals, uint32_t *err, cudaStream_t st) {
+    if (njobs <= 0) return cudaSuccess;
+    count_launch();
+    k_lengths_batch<<<njobs, 256, 0, st>>>(jobs, walk_len, totals, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_walks(const WalkJob *jobs, int njobs, const uint32_t *walk_len,
+                               uint32_t nwalks, uint32_t *order, uint32_t *err, cudaStream_t st) {
+    if (njobs <= 0 || nwalks == 0) return cudaSuccess;
+    static std::once_flag once;
+    static cudaError_t ea = cudaSuccess;
+    std::call_once(once, [] {
+        ea = cudaFuncSetAttribute((const void *)k_trace_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared);
+    });
+    if (ea != cudaSuccess) return ea;
+    count_launch(2);
+    k_order_len<<<1, 1024, 0, st>>>(walk_len, nwalks, order);
+    k_trace_batch<<<(nwalks + kBatchTraceWarps - 1) / kBatchTraceWarps, kBatchTraceWarps * 32, 0, st>>>(
+        jobs, njobs, order, nwalks, err);
     return cudaGetLastError();
 }
 

@@ -528,20 +528,27 @@ class Batch:
                                      ctypes.byref(b), ctypes.byref(tot)), "mpn_batch_info")
         return {"H": H.value, "W": W.value, "dist_bits": b.value, "total_cells": tot.value}
 
-    def result(self, ticket: int, n_starts: int, want_dist: bool = True):
-        """(dist or None, Paths, layers) of a finished grid, on the host."""
+    def result(self, ticket: int, n_starts: int, want_dist: bool = True, cells=None,
+               offsets=None, status=None):
+        """(dist or None, Paths, layers) of a finished grid. The path arrays
+        go into the given buffers when passed (numpy arrays or torch tensors,
+        host -- page-locked is fastest -- or device; cells must hold the
+        grid's total path cells, offsets n_starts + 1 uint64, status n_starts
+        int8), else into new host arrays."""
         inf = self.info(ticket)
         dist = None
         if want_dist:
             dist = np.empty((inf["H"], inf["W"]), np.uint16 if inf["dist_bits"] == 16 else np.uint32)
-        off = np.zeros(n_starts + 1, np.uint64)
-        cells = np.zeros(max(inf["total_cells"], 1), np.uint32)
-        status = np.zeros(max(n_starts, 1), np.int8)
+        total = inf["total_cells"]
+        off = np.empty(n_starts + 1, np.uint64) if offsets is None else offsets
+        cl = np.empty(max(total, 1), np.uint32) if cells is None else cells
+        sts = np.empty(max(n_starts, 1), np.int8) if status is None else status
+        cap = int(cl.numel() if hasattr(cl, "numel") else cl.size)
         layers = ctypes.c_uint32(0)
         _check(load().mpn_batch_result(self.h, ticket, _ptr(dist)[0] if dist is not None else None,
-                                       _ptr(off)[0], _ptr(cells)[0], cells.size, _ptr(status)[0],
+                                       _ptr(off)[0], _ptr(cl)[0], cap, _ptr(sts)[0],
                                        ctypes.byref(layers)), "mpn_batch_result")
-        return dist, Paths(off, cells[:inf["total_cells"]], status[:n_starts]), int(layers.value)
+        return dist, Paths(off, cl[:total], sts[:n_starts]), int(layers.value)
 
     def release(self, ticket: int):
         _check(load().mpn_batch_release(self.h, ticket), "mpn_batch_release")

@@ -59,9 +59,18 @@ def _count(a) -> int:
     return int(a.numel()) if hasattr(a, "numel") else int(np.asarray(a).size)
 
 
+def _own(a):
+    """A host numpy copy of an array or tensor view."""
+    return np.array(a.numpy() if hasattr(a, "numpy") else a, copy=True)
+
+
 def serve(batch: Batch, requests: list, round_sweeps: int = 64, keep_results: bool = False,
-          clock=time.perf_counter) -> ServeReport:
-    """Run every request through the batch as it arrives; returns latencies."""
+          clock=time.perf_counter, staging=None) -> ServeReport:
+    """Run every request through the batch as it arrives; returns latencies.
+    staging: optional (cells, offsets, status) host buffers (page-locked is
+    fastest), each large enough for any one response; every response is
+    downloaded into them (and copied out when kept) instead of into freshly
+    allocated arrays."""
     rep = ServeReport()
     order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
     waiting = collections.deque()
@@ -89,7 +98,15 @@ def serve(batch: Batch, requests: list, round_sweeps: int = 64, keep_results: bo
                     continue
                 i = in_flight.pop(tk)
                 if st == MPN_BATCH_DONE:
-                    _, paths, _ = batch.result(tk, _count(requests[i].starts), want_dist=False)
+                    n = _count(requests[i].starts)
+                    if staging is not None:
+                        _, paths, _ = batch.result(tk, n, want_dist=False, cells=staging[0],
+                                                   offsets=staging[1], status=staging[2])
+                        if keep_results:
+                            paths = type(paths)(_own(paths.offsets), _own(paths.cells),
+                                                _own(paths.status))
+                    else:
+                        _, paths, _ = batch.result(tk, n, want_dist=False)
                     if keep_results:
                         rep.results[i] = paths
                 else:

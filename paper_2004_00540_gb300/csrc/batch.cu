@@ -15,6 +15,7 @@
 // The per-tile work is wave::visit_tile, the same as the single-grid kernel.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -54,12 +55,14 @@ struct BatchCtl {
 struct BatchParams {
     MazeDesc *descs;
     uint32_t *tile_maze;    // global tile id -> slot
-    uint32_t *queued;       // global tile id -> 1 + last sweep queued for
-    uint32_t *lists;        // 3 lists of max_tiles entries
+    uint32_t *stamps;       // kStampSlots arrays of max_tiles: 1 + sweep the tile is queued for
+    uint32_t *done;         // global tile id -> 1 + last sweep whose visit of it finished
+    uint32_t *lists;        // kListSlots lists of max_tiles entries (1 + global tile id)
     uint32_t max_tiles;
     BatchCtl *bc;
     uint32_t round_sweeps;  // 0 = until every grid converged
     uint32_t spin_limit;
+    uint32_t lookahead;     // 1: blocks waiting at a sweep's end run ready tiles of the next
 };
 
 struct SeedJob {
@@ -68,16 +71,30 @@ struct SeedJob {
     const uint32_t *targets;
 };
 
+// Queue global tile gt of grid `slot` for sweep s unless it is queued already
+// (the list entry holds 1 + gt, so a block waiting at the end of the previous
+// sweep can poll it).
+__device__ __forceinline__ void push_gt_b(const BatchParams &p, uint32_t slot, uint32_t gt, uint32_t s) {
+    if (atomicMax(p.stamps + (size_t)(s % kStampSlots) * p.max_tiles + gt, s + 1) < s + 1) {
+        const uint32_t sl = s % kListSlots;
+        const uint32_t i = atomicAdd(&p.bc->c.list_len[sl], 1u);
+        wave::st_relaxed(p.lists + (size_t)sl * p.max_tiles + i, gt + 1u);
+        atomicMax(&p.descs[slot].last_push, s + 1);
+    }
+}
+
 __device__ __forceinline__ void push_tile_b(const BatchParams &p, const MazeDesc &d, uint32_t slot,
                                             int ty, int tx, uint32_t s) {
     if (ty < 0 || tx < 0 || ty >= d.nty || tx >= d.ntx) return;
-    const uint32_t gt = d.tile_base + (uint32_t)(ty * d.ntx + tx);
-    if (atomicMax(p.queued + gt, s + 1) < s + 1) {
-        const uint32_t sl = s % 3;
-        const uint32_t i = atomicAdd(&p.bc->c.list_len[sl], 1u);
-        p.lists[(size_t)sl * p.max_tiles + i] = gt;
-        atomicMax(&p.descs[slot].last_push, s + 1);
-    }
+    push_gt_b(p, slot, d.tile_base + (uint32_t)(ty * d.ntx + tx), s);
+}
+
+// Take entry i of a tile list: the global tile id (-1 if never written), and
+// clear the entry for the list slot's next use.
+__device__ __forceinline__ int take_entry_b(uint32_t *list, uint32_t i) {
+    const uint32_t e = ld_relaxed(list + i);
+    if (e) wave::st_relaxed(list + i, 0u);
+    return (int)e - 1;
 }
 
 // The tile of grid d that frontier cells in border zone z (one FB_* bit) of
@@ -135,72 +152,130 @@ __global__ void k_batch_seed(BatchParams p, const SeedJob *jobs) {
 
 // The round's sweeps over every admitted grid's queued tiles. As in the
 // single-grid kernel, entries 0 .. blocks - 1 of a sweep's list go one per
-// block without an atomic, and a visit's queue pushes are split across the
-// next visit (stamp after the visit, append after the next visit's layers).
+// block without an atomic, a visit's queue pushes are split across the next
+// visit (stamp after the visit, append after the next visit's layers), and a
+// block that has arrived at the end of a sweep runs tiles of the next sweep
+// whose 3 x 3 neighbourhood (within their grid) has finished the sweep. A
+// round's last sweep (the sweep budget) has no lookahead, so a round ends
+// with every visit of its sweeps done and nothing run ahead.
 template <int RXW, int R, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p) {
     __shared__ wave::VisitSmem<RXW, NW> sm;
     __shared__ int s_tile;
-    __shared__ unsigned s_mask[2], s_lastj[2], s_done, s_ok;
+    __shared__ unsigned s_mask[2], s_lastj[2], s_done;
     __shared__ uint32_t s_len;   // length of this sweep's list
+    __shared__ int s_dec[2];     // end of sweep, by poll parity: -3 stop, -2 wait, -1 go on, >= 0 run tile
+    __shared__ int s_done_t;     // visited tile whose done stamp is not out yet (-1: none)
+    __shared__ uint32_t s_done_v;
     Ctl *ctl = &p.bc->c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned vq = 0u;
     unsigned long long blk_visits = 0;
+    int pend_mine = -1;          // thread 0: list index claimed while waiting, not yet run
     const uint32_t s0 = ld_acquire(&p.bc->next_sweep);
     const uint32_t G = gridDim.x;
+    const size_t MT = p.max_tiles;
     sm.zero_pad();   // (the first barrier below publishes it)
     if (threadIdx.x == 0) {
         // the round's first sweep; later sweeps read their list length and
-        // first entry right after the grid barrier, with the end-of-round test
-        s_len = ld_acquire(&ctl->list_len[s0 % 3]);
-        s_tile = (blockIdx.x < s_len) ? (int)ld_relaxed(p.lists + (size_t)(s0 % 3) * p.max_tiles + blockIdx.x) : -1;
+        // first entry after the grid barrier, with the end-of-round test
+        s_len = ld_acquire(&ctl->list_len[s0 % kListSlots]);
+        s_tile = (blockIdx.x < s_len) ? take_entry_b(p.lists + (size_t)(s0 % kListSlots) * MT, blockIdx.x) : -1;
+        s_done_t = -1;
     }
     __syncthreads();
 
-    for (uint32_t s = s0;; ++s) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            ctl->work[(s + 2) % 3] = 0u;
-            ctl->list_len[(s + 2) % 3] = 0u;
+    // one thread: publish the done stamp of the last visited tile (release:
+    // the visit's writes, block barriers before, come with it)
+    auto publish_done = [&]() {
+        const int dt = s_done_t;
+        if (dt >= 0) {
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p.done + dt), "r"(s_done_v) : "memory");
+            s_done_t = -1;
         }
-        const uint32_t *list = p.lists + (size_t)(s % 3) * p.max_tiles;
-        unsigned *work = &ctl->work[s % 3];
+    };
+    auto hook = [&]() {
+        if (threadIdx.x == 32) publish_done();
+    };
+    // one visit of global tile t in sweep sv (an entry outside its grid's
+    // tile range, which the queue never holds, is skipped); returns the
+    // visit's first layer
+    auto visit = [&](int t, uint32_t sv, uint32_t *fmask, unsigned *lastj, uint32_t *slot_out,
+                     const MazeDesc **dout, int *ty, int *tx, bool with_hook) {
+        const uint32_t slot = __ldg(p.tile_maze + t);
+        const MazeDesc &dref = p.descs[slot];
+        // defensive: a list entry must lie in its grid's tile range
+        const bool valid = (uint32_t)t - dref.tile_base < (uint32_t)(dref.ntx * dref.nty);
+        wave::Visit v;
+        v.g = dref.g;
+        v.dist_bits = dref.dist_bits;
+        v.TY = dref.TY;
+        v.TXW = dref.TXW;
+        v.k = dref.k;
+        const int ntx = dref.ntx;
+        const uint32_t local = (uint32_t)t - dref.tile_base;
+        v.ty = (int)(local / (uint32_t)ntx);
+        v.tx = (int)(local - (uint32_t)v.ty * ntx);
+        v.l0 = (sv - dref.start_sweep) * (uint32_t)v.k;
+        const uint32_t maxl = dref.max_layers;
+        v.jmax = v.k;
+        if (maxl && v.l0 + (uint32_t)v.k > maxl) v.jmax = (int)(maxl - v.l0);
+        v.par = (int)(sv & 1u);
+        *fmask = 0u;
+        *lastj = 0u;
+        if (valid) {
+            if (with_hook) wave::visit_tile<RXW, R, NW>(v, sm, &p.descs[slot].err, fmask, lastj, wave::LogSink(), nullptr, hook);
+            else wave::visit_tile<RXW, R, NW>(v, sm, &p.descs[slot].err, fmask, lastj);
+        }
+        if (maxl && v.l0 + (uint32_t)v.k >= maxl) *fmask = 0u;   // fixed depth reached
+        *slot_out = slot;
+        *dout = &dref;
+        *ty = v.ty;
+        *tx = v.tx;
+        return v.l0;
+    };
+
+    for (uint32_t s = s0;; ++s) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && s > s0) {
+            // list slot (s + 3) % 4 last served sweep s - 1 and next serves s + 3
+            const uint32_t r = (s + 3) % kListSlots;
+            ctl->work[r] = 0u;
+            ctl->list_len[r] = 0u;
+        }
+        uint32_t *list = p.lists + (size_t)(s % kListSlots) * MT;
+        unsigned *work = &ctl->work[s % kListSlots];
         const uint32_t len = s_len;
         int t = s_tile;
+        if (t < 0 && threadIdx.x == 0) {
+            const uint32_t i = pend_mine >= 0 ? (uint32_t)pend_mine : G + atomicAdd(work, 1u);
+            pend_mine = -1;
+            s_tile = (i < len) ? take_entry_b(list, i) : -1;
+        }
+        __syncthreads();
+        t = s_tile;
         const uint32_t stamp = s + 2u;            // queued for sweep s + 1
-        const uint32_t sl1 = (s + 1u) % 3u;
+        const uint32_t sl1 = (s + 1u) % kListSlots;
+        uint32_t *stamps1 = p.stamps + (size_t)((s + 1u) % kStampSlots) * MT;
         int64_t pend_gt = -1;                     // lanes 0..8: global tile of a push in flight
         uint32_t pend_old = 0u, pend_slot = 0u;   // its stamp before the atomicMax, its grid
         while (t >= 0) {
             uint32_t next_i = 0;
             vq ^= 1u;
             if (threadIdx.x == 0) {
-                next_i = G + atomicAdd(work, 1u);
+                if (pend_mine >= 0) {
+                    next_i = (uint32_t)pend_mine;
+                    pend_mine = -1;
+                } else {
+                    next_i = G + atomicAdd(work, 1u);
+                }
                 s_mask[vq] = 0u;
                 s_lastj[vq] = 0u;
             }
-            const uint32_t slot = __ldg(p.tile_maze + t);
-            const MazeDesc &dref = p.descs[slot];
-            // defensive: a list entry must lie in its grid's tile range
-            const bool valid = (uint32_t)t - dref.tile_base < (uint32_t)(dref.ntx * dref.nty);
-            wave::Visit v;
-            v.g = dref.g;
-            v.dist_bits = dref.dist_bits;
-            v.TY = dref.TY;
-            v.TXW = dref.TXW;
-            v.k = dref.k;
-            const int ntx = dref.ntx;
-            const uint32_t local = (uint32_t)t - dref.tile_base;
-            v.ty = (int)(local / (uint32_t)ntx);
-            v.tx = (int)(local - (uint32_t)v.ty * ntx);
-            v.l0 = (s - dref.start_sweep) * (uint32_t)v.k;
-            const uint32_t maxl = dref.max_layers;
-            v.jmax = v.k;
-            if (maxl && v.l0 + (uint32_t)v.k > maxl) v.jmax = (int)(maxl - v.l0);
-            v.par = (int)(s & 1u);
-            uint32_t fmask = 0u;
-            unsigned lastj = 0u;
-            if (valid) wave::visit_tile<RXW, R, NW>(v, sm, &p.descs[slot].err, &fmask, &lastj);
-            if (maxl && v.l0 + (uint32_t)v.k >= maxl) fmask = 0u;   // fixed depth reached
+            uint32_t fmask, slot;
+            unsigned lastj;
+            const MazeDesc *dp;
+            int ty, tx;
+            const uint32_t l0 = visit(t, s, &fmask, &lastj, &slot, &dp, &ty, &tx, true);
             uint32_t pend_i = 0u;
             const bool pend_new = pend_gt >= 0 && pend_old < stamp;   // previous visit's push
             if (pend_new) pend_i = atomicAdd(&ctl->list_len[sl1], 1u);
@@ -208,48 +283,181 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             if (lastj) atomicMax(&s_lastj[vq], lastj);
             if (threadIdx.x == 0) {
                 ++blk_visits;
-                s_tile = (next_i < len) ? (int)ld_relaxed(list + next_i) : -1;
+                s_tile = (next_i < len) ? take_entry_b(list, next_i) : -1;
             }
             __syncthreads();
+            if (threadIdx.x == 0) {
+                s_done_t = t;   // published by the next visit's hook, or before the block waits
+                s_done_v = s + 1u;
+            }
             if (threadIdx.x < 9) {
                 if (pend_new) {
-                    p.lists[(size_t)sl1 * p.max_tiles + pend_i] = (uint32_t)pend_gt;
+                    wave::st_relaxed(p.lists + (size_t)sl1 * MT + pend_i, (uint32_t)pend_gt + 1u);
                     atomicMax(&p.descs[pend_slot].last_push, stamp);
                 }
                 // this visit's push for border zone threadIdx.x: stamp now, append later
                 const uint32_t zone = 1u << threadIdx.x;
-                pend_gt = (s_mask[vq] & zone) ? zone_tile_b(dref, v.ty, v.tx, zone) : -1;
+                pend_gt = (s_mask[vq] & zone) ? zone_tile_b(*dp, ty, tx, zone) : -1;
                 if (pend_gt >= 0) {
                     pend_slot = slot;
-                    pend_old = atomicMax(p.queued + pend_gt, stamp);
+                    pend_old = atomicMax(stamps1 + pend_gt, stamp);
                 }
-                if (threadIdx.x == 0 && s_lastj[vq])
-                    atomicMax(&p.descs[slot].maxl, v.l0 + s_lastj[vq]);
+                if (threadIdx.x == 0 && s_lastj[vq]) atomicMax(&p.descs[slot].maxl, l0 + s_lastj[vq]);
             }
             t = s_tile;
         }
         if (pend_gt >= 0 && pend_old < stamp) {   // the sweep's last visit
             const uint32_t i = atomicAdd(&ctl->list_len[sl1], 1u);
-            p.lists[(size_t)sl1 * p.max_tiles + i] = (uint32_t)pend_gt;
+            wave::st_relaxed(p.lists + (size_t)sl1 * MT + i, (uint32_t)pend_gt + 1u);
             atomicMax(&p.descs[pend_slot].last_push, stamp);
         }
 
-        if (!wave::grid_barrier(ctl, (s + 1 - s0) * gridDim.x, p.spin_limit, &s_ok)) return;
+        // ---- end of sweep s: arrive, then run ready tiles of sweep s + 1
+        // until every block has arrived ----
+        const unsigned target = (s + 1 - s0) * G;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            // one read gives the end-of-round test, the next sweep's list
-            // length and (alongside) this block's first entry of it
-            const uint32_t nlen = ld_acquire(&ctl->list_len[(s + 1) % 3]);
-            const uint32_t *nlist = p.lists + (size_t)((s + 1) % 3) * p.max_tiles;
-            const int first = (blockIdx.x < p.max_tiles) ? (int)ld_relaxed(nlist + blockIdx.x) : -1;
-            const unsigned done = (nlen == 0u) || (p.round_sweeps && s + 1 - s0 >= p.round_sweeps);
+            publish_done();
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
+        }
+        const bool last = p.round_sweeps && s + 1 - s0 >= p.round_sweeps;   // the round's last sweep
+        const bool look = p.lookahead && !last;
+        uint32_t *list1 = p.lists + (size_t)sl1 * MT;
+        const uint32_t *stamps0 = p.stamps + (size_t)(s % kStampSlots) * MT;
+        bool fixed_taken = false;   // thread 0: this block's first entry of s + 1 ran
+        unsigned spins = 0;         // thread 0: idle polls
+        int toggle = 0;
+        for (unsigned it = 0;; it ^= 1u) {
+            if (warp == 0) {
+                int dec = -2, cand = -1, cidx = -1;
+                if (lane == 0) {
+                    int fe = -1, me = -1;
+                    if (look) {
+                        if (!fixed_taken) fe = (int)ld_relaxed(list1 + blockIdx.x) - 1;
+                        if (pend_mine >= 0 && (uint32_t)pend_mine < MT) me = (int)ld_relaxed(list1 + pend_mine) - 1;
+                    }
+                    if (ld_acquire(&ctl->bar_count) >= target) {
+                        dec = -1;
+                    } else if (look) {
+                        if (fe >= 0 && (me < 0 || !toggle)) {
+                            cand = fe;
+                            cidx = (int)blockIdx.x;
+                        } else if (me >= 0) {
+                            cand = me;
+                            cidx = pend_mine;
+                        }
+                        toggle ^= 1;
+                        if (pend_mine < 0 && (fixed_taken || fe < 0 || toggle))
+                            pend_mine = (int)(G + atomicAdd(&ctl->work[sl1], 1u));
+                    }
+                }
+                dec = __shfl_sync(0xffffffffu, dec, 0);
+                cand = __shfl_sync(0xffffffffu, cand, 0);
+                if (dec == -2 && cand >= 0) {
+                    // lanes 0..8: has the neighbour (in the candidate's grid) that
+                    // sweep s still had to visit finished it?
+                    bool ok = true;
+                    if (lane < 9) {
+                        const MazeDesc &cd = p.descs[__ldg(p.tile_maze + cand)];
+                        const uint32_t local = (uint32_t)cand - cd.tile_base;
+                        const int cy = (int)(local / (uint32_t)cd.ntx), cx = (int)(local - (uint32_t)cy * cd.ntx);
+                        const int ny = cy + lane / 3 - 1, nx = cx + lane % 3 - 1;
+                        if (local < (uint32_t)(cd.ntx * cd.nty) && ny >= 0 && nx >= 0 && ny < cd.nty && nx < cd.ntx) {
+                            const uint32_t n = cd.tile_base + (uint32_t)(ny * cd.ntx + nx);
+                            const uint32_t st = ld_relaxed(stamps0 + n), dn = ld_acquire(p.done + n);
+                            ok = st != s + 1u || dn >= s + 1u;
+                        }
+                    }
+                    if (__all_sync(0xffffffffu, ok)) {
+                        dec = cand;
+                        if (lane == 0) {
+                            wave::st_relaxed(list1 + cidx, 0u);
+                            if (cidx == (int)blockIdx.x && !fixed_taken) fixed_taken = true;
+                            else pend_mine = -1;
+                        }
+                    }
+                }
+                if (lane == 0) {
+                    if (dec == -2) {
+                        ++spins;
+                        if ((spins & 63u) == 0u && (ld_acquire(&ctl->err) & ERR_TIMEOUT)) dec = -3;
+                        if (spins > p.spin_limit) {
+                            atomicOr(&ctl->err, ERR_TIMEOUT);
+                            dec = -3;
+                        }
+                        if (dec == -2 && spins > 8) __nanosleep(32);
+                    }
+                    s_dec[it] = dec;   // (read two polls ago, before the last block barrier)
+                }
+            }
+            __syncthreads();
+            const int d = s_dec[it];
+            if (d == -3) return;   // a wait ran out (recorded): every block stops
+            if (d == -1) break;    // every block has arrived
+            if (d == -2) continue;
+            // ---- a visit of global tile d in sweep s + 1 ----
+            vq ^= 1u;
+            if (threadIdx.x == 0) {
+                s_mask[vq] = 0u;
+                s_lastj[vq] = 0u;
+            }
+            uint32_t fmask, slot;
+            unsigned lastj;
+            const MazeDesc *dp;
+            int ty, tx;
+            const uint32_t l1 = visit(d, s + 1u, &fmask, &lastj, &slot, &dp, &ty, &tx, false);
+            if (fmask) atomicOr(&s_mask[vq], fmask);
+            if (lastj) atomicMax(&s_lastj[vq], lastj);
+            if (threadIdx.x == 0) ++blk_visits;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_done_t = d;
+                s_done_v = s + 2u;
+                publish_done();   // the block waits anyway: out at once
+                spins = 0;
+            }
+            if (threadIdx.x < 9) {   // what it reaches goes to sweep s + 2 at once
+                const uint32_t zone = 1u << threadIdx.x;
+                if (s_mask[vq] & zone) {
+                    const int64_t gt2 = zone_tile_b(*dp, ty, tx, zone);
+                    if (gt2 >= 0) push_gt_b(p, slot, (uint32_t)gt2, s + 2u);
+                }
+                if (threadIdx.x == 0 && s_lastj[vq]) atomicMax(&p.descs[slot].maxl, l1 + s_lastj[vq]);
+            }
+        }
+
+        if (threadIdx.x == 0) {
+            // one read gives the end-of-round test and the next sweep's list
+            // length; the block's own entry of it comes alongside
+            const uint32_t nlen = ld_relaxed(&ctl->list_len[sl1]);
+            const uint32_t fe = fixed_taken ? 0u : ld_relaxed(list1 + blockIdx.x);
+            const unsigned done = (nlen == 0u) || last;
             if (done && blockIdx.x == 0) {
                 p.bc->next_sweep = s + 1;
                 ctl->sweeps = s + 1 - s0;
+                // list slots the next round pushes into start empty; its first
+                // list (s + 1) is kept, with a fresh claim counter
+                for (uint32_t q = 0; q < (uint32_t)kListSlots; ++q) {
+                    ctl->work[q] = 0u;
+                    if (q != sl1) ctl->list_len[q] = 0u;
+                }
             }
             if (done && blk_visits) atomicAdd(&ctl->visits, blk_visits);
             s_done = done;
             s_len = nlen;
-            s_tile = (blockIdx.x < nlen) ? first : -1;
+            int first = -1;
+            if (!done) {   // (a finished round leaves list s + 1 to the next round)
+                if (!fixed_taken && blockIdx.x < nlen && fe) {
+                    first = (int)fe - 1;
+                    wave::st_relaxed(list1 + blockIdx.x, 0u);
+                }
+                if (first < 0 && pend_mine >= 0) {
+                    if ((uint32_t)pend_mine < nlen) first = take_entry_b(list1, (uint32_t)pend_mine);
+                    pend_mine = -1;
+                }
+                if (pend_mine >= 0 && (uint32_t)pend_mine >= nlen) pend_mine = -1;   // never written
+            }
+            s_tile = first;
         }
         __syncthreads();
         if (s_done) return;
@@ -281,7 +489,7 @@ __global__ void k_check_inputs(const uint32_t *free_bits, int H, int W, int P,
 // counter for the round's first sweep and a clear error word.
 __global__ void k_round_prep(BatchCtl *bc) {
     const uint32_t s = bc->next_sweep;
-    bc->c.work[s % 3] = 0u;
+    bc->c.work[s % kListSlots] = 0u;
     bc->c.err = 0u;
     bc->c.bar_count = 0u;   // the round's barriers count from zero
 }
@@ -394,7 +602,7 @@ struct mpn_batch {
     size_t arena_bytes = 0;
     RangeAlloc mem, tiles;
     MazeDesc *d_descs = nullptr;
-    uint32_t *d_tile_maze = nullptr, *d_queued = nullptr, *d_lists = nullptr;
+    uint32_t *d_tile_maze = nullptr, *d_stamps = nullptr, *d_done = nullptr, *d_lists = nullptr;
     BatchCtl *d_bc = nullptr;
     SeedJob *d_jobs = nullptr;
     MazeDesc *h_descs = nullptr;      // pinned mirror for readback
@@ -413,7 +621,7 @@ struct mpn_batch {
     uint64_t *d_totals = nullptr, *h_totals = nullptr;
     uint32_t *d_walk_len = nullptr, *d_order = nullptr;
     size_t walk_cap = 0;
-    std::map<uint32_t, cudaGraphExec_t> graphs;   // one captured round per max_sweeps value
+    std::map<uint64_t, cudaGraphExec_t> graphs;   // one captured round per (max_sweeps, lookahead)
     bool use_graph = true;
     float last_round_ms = 0.f;
     uint64_t rounds = 0, sweeps_total = 0;
@@ -499,15 +707,18 @@ mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream
     e = cudaMalloc(&b->arena, budget_bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_descs, b->max_slots * sizeof(MazeDesc));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tile_maze, (size_t)b->max_tiles * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_queued, (size_t)b->max_tiles * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_lists, (size_t)b->max_tiles * 3 * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_stamps, (size_t)b->max_tiles * kStampSlots * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_done, (size_t)b->max_tiles * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_lists, (size_t)b->max_tiles * kListSlots * 4);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bc, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_jobs, b->max_slots * sizeof(SeedJob));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_descs, b->max_slots * sizeof(MazeDesc));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_bc, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_jobs, b->max_slots * sizeof(SeedJob));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_flag, sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queued, 0, (size_t)b->max_tiles * 4, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_stamps, 0, (size_t)b->max_tiles * kStampSlots * 4, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, (size_t)b->max_tiles * 4, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_lists, 0, (size_t)b->max_tiles * kListSlots * 4, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bc, 0, sizeof(BatchCtl), b->stream);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
@@ -666,7 +877,8 @@ static cudaError_t run_round(mpn_batch *b, const BatchParams &p) {
         count_launch(2);
         return enqueue_round(b, p);
     }
-    auto it = b->graphs.find(p.round_sweeps);
+    const uint64_t key = ((uint64_t)p.round_sweeps << 1) | (p.lookahead & 1u);
+    auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         cudaStream_t cs = nullptr;
         cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
@@ -692,7 +904,7 @@ static cudaError_t run_round(mpn_batch *b, const BatchParams &p) {
             count_launch(2);
             return enqueue_round(b, p);
         }
-        it = b->graphs.emplace(p.round_sweeps, ge).first;
+        it = b->graphs.emplace(key, ge).first;
     }
     count_launch(2);
     return cudaGraphLaunch(it->second, b->stream);
@@ -853,6 +1065,12 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, 
         for (auto &kv : b->mazes)
             if (kv.second.slot == b->h_jobs[j].slot && kv.second.state == MState::Running) m = &kv.second;
         if (!m) continue;
+        // queue stamps and done stamps of its tile range start at zero (the
+        // range may have served an earlier grid)
+        for (int q = 0; q < kStampSlots; ++q)
+            B_TRY(cudaMemsetAsync(b->d_stamps + (size_t)q * b->max_tiles + m->tile_base, 0,
+                                  (size_t)m->ntiles * 4, st));
+        B_TRY(cudaMemsetAsync(b->d_done + m->tile_base, 0, (size_t)m->ntiles * 4, st));
         const unsigned nb = (m->ntiles + 255) / 256;
         count_launch();
         k_fill_u32<<<nb < 1024 ? nb : 1024, 256, 0, st>>>(b->d_tile_maze + m->tile_base, m->ntiles, m->slot);
@@ -861,12 +1079,16 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, 
     BatchParams p{};
     p.descs = b->d_descs;
     p.tile_maze = b->d_tile_maze;
-    p.queued = b->d_queued;
+    p.stamps = b->d_stamps;
+    p.done = b->d_done;
     p.lists = b->d_lists;
     p.max_tiles = b->max_tiles;
     p.bc = b->d_bc;
     p.round_sweeps = max_sweeps;
     p.spin_limit = 1u << 24;
+    p.lookahead = 1;
+    // (test hook: MPN_TEST_NO_LOOKAHEAD=1 makes blocks only wait at a sweep's end)
+    if (const char *ev = getenv("MPN_TEST_NO_LOOKAHEAD")) p.lookahead = (ev[0] == '1') ? 0u : 1u;
     if (njobs > 0) {
         B_TRY(cudaMemcpyAsync(b->d_jobs, b->h_jobs, njobs * sizeof(SeedJob), cudaMemcpyHostToDevice, st));
         count_launch();
@@ -1024,7 +1246,8 @@ void mpn_batch_destroy(mpn_batch *b) {
     cudaFree(b->arena);
     cudaFree(b->d_descs);
     cudaFree(b->d_tile_maze);
-    cudaFree(b->d_queued);
+    cudaFree(b->d_stamps);
+    cudaFree(b->d_done);
     cudaFree(b->d_lists);
     cudaFree(b->d_bc);
     cudaFree(b->d_jobs);

@@ -167,3 +167,17 @@ def test_serve_on_the_real_engine_matches_oracle_alone_and_in_the_mix():
                       round_sweeps=4, keep_results=True)
     assert np.array_equal(alone.results[0].cells, rep.results[5].cells)
     assert np.array_equal(alone.results[0].offsets, rep.results[5].offsets)
+
+
+def test_batch_without_lookahead_same_results(monkeypatch):
+    """Blocks that only wait at a sweep's end (lookahead off, a test hook)
+    give the same paths as the default, where they run ready tiles of the
+    next sweep meanwhile; both equal the oracle's."""
+    ws = small_members(10, side_hi=420, base_seed=150)
+    monkeypatch.setenv("MPN_TEST_NO_LOOKAHEAD", "1")
+    with pkg.Batch(1 << 30) as b:
+        tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
+        b.run(3)                      # a short round, then the rest
+        b.run(0)
+        for tk, w in zip(tks, ws):
+            check(b, tk, w)

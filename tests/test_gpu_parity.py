@@ -386,6 +386,31 @@ def test_device_waits_run_out_then_context_recovers(hook, value, monkeypatch):
     assert np.array_equal(paths.cells, cells)
 
 
+@pytest.mark.parametrize("lookahead", ["0", "1"])
+def test_lookahead_on_and_off_equal_oracle(lookahead, monkeypatch):
+    """Blocks waiting at the end of a sweep either only wait (hook "1") or run
+    tiles of the next sweep whose neighbourhood has finished (default): the
+    same distances and paths, equal to the oracle's, on a maze (few tiles per
+    sweep) and a Bernoulli grid (many), at two depths and a fixed layer cap."""
+    monkeypatch.setenv("MPN_TEST_NO_LOOKAHEAD", "1" if lookahead == "0" else "0")
+    maze = synth.dfs_maze(700, 900, 163)
+    cases = [rand_case(1500, 1300, 0.3, 4, 30, 161), (maze, synth.sample_free(maze, 2, 164),
+                                                       synth.sample_free(maze, 30, 165))]
+    for m, t, s in cases:
+        for depth in (8, 24):
+            with pkg.Planner(m, pkg.MPN_DIST_U32) as pl:
+                pl.set_tuning(0, depth)
+                d, L = oracle.bfs(m, t)
+                assert pl.propagate(t) == L
+                assert np.array_equal(widen(pl.distances()), d)
+                paths = pl.trace(s)
+                off, cells, status = oracle.trace(m, d, s)
+                assert np.array_equal(paths.cells, cells) and np.array_equal(paths.offsets, off)
+                dL, _ = oracle.bfs(m, t, max_layers=L // 3 + 1)
+                pl.propagate(t, max_layers=L // 3 + 1)
+                assert np.array_equal(widen(pl.distances()), dL)
+
+
 def test_autotune_records_choice_and_stays_exact():
     m, t, s = rand_case(1500, 1400, 0.3, 6, 40, 77)
     with pkg.Planner(m) as pl:

@@ -142,6 +142,7 @@ struct mpn_ctx {
 
     DevBuf free_bits, state, dist, ctl, tiles, mask_stage, log;
     DevBuf targets, starts, offsets, status, cells, activity, order;
+    DevBuf jump, segs;   // long walks: jump table (2 * H * W words), segments + counter
 
     int variant = 0, depth = 32;
     bool auto_tune = true;
@@ -208,7 +209,7 @@ __global__ void k_store_host(const unsigned char *__restrict__ src, unsigned cha
 namespace {
 
 // Mailbox layout (bytes): the control block, then a path total and an error word.
-constexpr size_t kMboxCtl = 0, kMboxTotal = 128, kMboxErr = 136, kMboxBytes = 256;
+constexpr size_t kMboxCtl = 0, kMboxTotal = 128, kMboxErr = 136, kMboxWalk = 140, kMboxBytes = 256;
 static_assert(sizeof(Ctl) <= kMboxTotal, "control block must fit the mailbox");
 
 cudaError_t store_host(mpn_ctx *c, void *dst_dev, const void *src, size_t bytes) {
@@ -679,7 +680,8 @@ mpn_status mpn_get_activity(mpn_ctx *c, uint32_t L, int32_t *dst, int32_t on_dev
 }
 
 static mpn_status trace_prepare(mpn_ctx *c, const uint32_t *starts, int32_t n,
-                                const uint32_t **ds, uint64_t *total, bool euclid = false) {
+                                const uint32_t **ds, uint64_t *total, bool euclid = false,
+                                uint32_t *walk_max = nullptr) {
     if (!c || n < 0 || (n > 0 && !starts)) return MPN_EINVAL;
     mpn_status st = finish_propagate(c);
     if (st != MPN_OK) return st;
@@ -695,6 +697,7 @@ static mpn_status trace_prepare(mpn_ctx *c, const uint32_t *starts, int32_t n,
     MPN_TRY(c->status.ensure((size_t)(n > 0 ? n : 1)));
     Ctl *ctl = (Ctl *)c->ctl.p;
     MPN_TRY(cudaMemsetAsync(&ctl->err, 0, sizeof(uint32_t), c->stream));
+    MPN_TRY(cudaMemsetAsync(&ctl->walk_max, 0, sizeof(uint32_t), c->stream));
     MPN_TRY(cudaMemsetAsync(c->offsets.p, 0, sizeof(uint64_t), c->stream));
     if (n > 0) {
         MPN_TRY(launch_trace_lengths(c->grid(), c->dist_bits, *ds, n, (uint64_t *)c->offsets.p,
@@ -707,9 +710,11 @@ static mpn_status trace_prepare(mpn_ctx *c, const uint32_t *starts, int32_t n,
     uint32_t err = 0;
     MPN_TRY(to_mbox(c, kMboxTotal, (uint64_t *)c->offsets.p + n, sizeof(uint64_t)));
     MPN_TRY(to_mbox(c, kMboxErr, &ctl->err, sizeof(uint32_t)));
+    MPN_TRY(to_mbox(c, kMboxWalk, &ctl->walk_max, sizeof(uint32_t)));
     MPN_TRY(cudaStreamSynchronize(c->stream));
     memcpy(total, c->mbox + kMboxTotal, sizeof(uint64_t));
     memcpy(&err, c->mbox + kMboxErr, sizeof(uint32_t));
+    if (walk_max) memcpy(walk_max, c->mbox + kMboxWalk, sizeof(uint32_t));
     if (err) return from_err_bits(err);
     return MPN_OK;
 }
@@ -729,7 +734,8 @@ static mpn_status trace_any(mpn_ctx *c, const uint32_t *starts, int32_t n, uint6
     if (!offsets || (n > 0 && !status)) return MPN_EINVAL;
     const uint32_t *ds = nullptr;
     uint64_t total = 0;
-    mpn_status st = trace_prepare(c, starts, n, &ds, &total, euclid);
+    uint32_t walk_max = 0;
+    mpn_status st = trace_prepare(c, starts, n, &ds, &total, euclid, &walk_max);
     if (st != MPN_OK) return st;
     MPN_TRY(copy_out(c, offsets, c->offsets.p, (size_t)(n + 1) * sizeof(uint64_t)));
     if (n > 0) MPN_TRY(copy_out(c, status, c->status.p, (size_t)n));
@@ -754,8 +760,27 @@ static mpn_status trace_any(mpn_ctx *c, const uint32_t *starts, int32_t n, uint6
         uint32_t *ord = nullptr;
         if (c->order.ensure((size_t)n * sizeof(uint32_t)) == cudaSuccess) ord = (uint32_t *)c->order.p;
         else cudaGetLastError();
-        MPN_TRY(launch_trace(c->grid(), c->dist_bits, ds, n, (const uint64_t *)c->offsets.p,
-                             (const int8_t *)c->status.p, dcells, ord, c->stream, &ctl->err));
+        // a walk far longer than the rest is split into segments walked side
+        // by side (a jump table finds their first cells), when there is room
+        bool split = false;
+        const uint64_t seg_cap = total / kSegLen + (uint64_t)n + 1;
+        if (walk_max > kLongWalk && seg_cap < 0xffffffffull) {
+            const size_t cells_n = (size_t)c->H * c->W;
+            if (c->jump.ensure(2 * cells_n * sizeof(uint32_t)) == cudaSuccess &&
+                c->segs.ensure(seg_cap * sizeof(WalkSeg) + 16) == cudaSuccess)
+                split = true;
+            else
+                cudaGetLastError();
+        }
+        if (split)
+            MPN_TRY(launch_trace_split(c->grid(), c->dist_bits, ds, n, (const uint64_t *)c->offsets.p,
+                                       (const int8_t *)c->status.p, dcells, ord, (uint32_t *)c->jump.p,
+                                       (WalkSeg *)c->segs.p, (uint32_t)seg_cap,
+                                       (uint32_t *)((char *)c->segs.p + seg_cap * sizeof(WalkSeg)),
+                                       c->stream, &ctl->err));
+        else
+            MPN_TRY(launch_trace(c->grid(), c->dist_bits, ds, n, (const uint64_t *)c->offsets.p,
+                                 (const int8_t *)c->status.p, dcells, ord, c->stream, &ctl->err));
     }
     MPN_TRY(cudaEventRecord(c->ev[5], c->stream));
     c->ev_trace = true;
@@ -882,7 +907,7 @@ void mpn_destroy(mpn_ctx *c) {
     if (c->out_pending && cudaEventSynchronize(c->ev_out) != cudaSuccess) cudaGetLastError();
     DevBuf *bufs[] = {&c->free_bits, &c->state, &c->log, &c->dist, &c->ctl, &c->tiles,
                       &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
-                      &c->cells, &c->activity, &c->order};
+                      &c->cells, &c->activity, &c->order, &c->jump, &c->segs};
     for (DevBuf *b : bufs) b->release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);

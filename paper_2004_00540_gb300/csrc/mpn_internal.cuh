@@ -33,6 +33,7 @@ struct Ctl {
     unsigned int max_layer;        // largest activation layer seen
     unsigned int sweeps;
     unsigned int plain_last;       // per-layer kernel: last layer that activated a cell
+    unsigned int walk_max;         // longest path (cells) of the last trace's starts, saturated
     unsigned long long visits;     // tile visits
     unsigned long long tile_layers;   // layers those visits ran (a stable region stops early)
     unsigned long long log_entries;   // activation-log entries written
@@ -196,6 +197,22 @@ cudaError_t launch_scan(uint64_t *offsets, int n, cudaStream_t st);
 cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
                          const uint64_t *offsets, const int8_t *status, uint32_t *cells,
                          uint32_t *order, cudaStream_t st, uint32_t *err);
+// Walks longer than kLongWalk cells are cut into segments of kSegLen steps,
+// walked side by side: the cell kSegLen steps further along every walk comes
+// from a jump table succ^kSegLen (succ = the next cell of the walk rule),
+// built by repeated squaring in `jump` (2 * H * W words of scratch). segs:
+// room for seg_cap segments (16 bytes each) and a counter at nseg.
+constexpr uint32_t kLongWalk = 8192;
+constexpr uint32_t kSegLen = 2048;
+struct WalkSeg {
+    uint32_t cell;    // first cell of the segment
+    uint32_t dstop;   // distance at which it ends (its last cell)
+    uint64_t out;     // where its first cell goes in the path output
+};
+cudaError_t launch_trace_split(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                               const uint64_t *offsets, const int8_t *status, uint32_t *cells,
+                               uint32_t *order, uint32_t *jump, WalkSeg *segs, uint32_t seg_cap,
+                               uint32_t *nseg, cudaStream_t st, uint32_t *err);
 cudaError_t launch_activity(const GridDev &g, int dist_bits, uint32_t L, int32_t *out,
                             cudaStream_t st);
 

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(1024) k_order(const uint64_t *__restrict__ off
 template <typename DT>
 __global__ void k_lengths(GridDev g, const uint32_t *__restrict__ starts, int n,
                           uint64_t *__restrict__ offsets, int8_t *__restrict__ status,
-                          uint32_t *err) {
+                          uint32_t *err, uint32_t *walk_max) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) offsets[0] = 0ull;
     if (i >= n) return;
@@ -95,6 +95,9 @@ __global__ void k_lengths(GridDev g, const uint32_t *__restrict__ starts, int n,
     }
     offsets[i + 1] = len;
     status[i] = stt;
+    // the longest path, one atomic per warp
+    const uint32_t m = __reduce_max_sync(__activemask(), len > 0xffffffffull ? 0xffffffffu : (uint32_t)len);
+    if ((threadIdx.x & 31) == __ffs(__activemask()) - 1 && m) atomicMax(walk_max, m);
 }
 
 // In-place inclusive scan of a[1..n] by one block: chunks of blockDim * 8
@@ -151,14 +154,16 @@ __device__ __forceinline__ void block_scan_inplace(uint64_t *a, int n) {
 
 __global__ void k_scan(uint64_t *a, int n) { block_scan_inplace(a, n); }
 
-// One walk by the calling warp (all 32 lanes), from start c (free, reached)
-// down to a target. wb: the warp's window buffer, kW x (kW + 1) elements of
-// DT. CELLS: the path's cells go to cells[o0], cells[o0 + 1], ...; *end gets
-// the linear index of the cell the walk ends at. False if the plane is not a
-// distance plane (no neighbour one step closer; ERR_TRACE recorded).
+// One walk by the calling warp (all 32 lanes), from cell c (free, reached)
+// down to distance dstop (0: a target). wb: the warp's window buffer, kW x
+// (kW + 1) elements of DT. CELLS: the walk's cells go to cells[o0], cells[o0 +
+// 1], ...; *end gets the linear index of the cell the walk ends at. False if
+// the plane is not a distance plane (no neighbour one step closer; ERR_TRACE
+// recorded).
 template <typename DT, int kW, bool CELLS>
 __device__ __forceinline__ bool walk_path(const GridDev &g, uint32_t c, uint64_t o0, DT *wb,
-                                          uint32_t *__restrict__ cells, uint32_t *err, uint32_t *end) {
+                                          uint32_t *__restrict__ cells, uint32_t *err, uint32_t *end,
+                                          uint32_t dstop = 0u) {
     constexpr int kP = kW + 1;
     const int lane = threadIdx.x & 31;
     const DT *dist = reinterpret_cast<const DT *>(g.dist);
@@ -182,7 +187,7 @@ __device__ __forceinline__ bool walk_path(const GridDev &g, uint32_t c, uint64_t
     uint32_t d = (uint32_t)dist[c];
     if (CELLS && lane == 0) cells[o] = c;
     int ddy = 0, ddx = 0;   // how far the walk moved in the last window
-    while (d > 0) {
+    while (d > dstop) {
         // the next window reaches further in the direction the walk has been
         // heading: along an axis on which it moved at least kW / 4 cells in
         // the last window, the current cell sits a quarter window in from the
@@ -215,8 +220,8 @@ __device__ __forceinline__ bool walk_path(const GridDev &g, uint32_t c, uint64_t
         }
         __syncwarp();
         int ly = oy, lx = ox;
-        while (d > 0 && ly >= 1 && ly <= kW - 2 && lx >= 1 && lx <= kW - 2) {
-            if (d >= 2 && ly >= 2 && ly <= kW - 3 && lx >= 2 && lx <= kW - 3) {
+        while (d > dstop && ly >= 1 && ly <= kW - 2 && lx >= 1 && lx <= kW - 2) {
+            if (d >= dstop + 2u && ly >= 2 && ly <= kW - 3 && lx >= 2 && lx <= kW - 3) {
                 // two steps at once: lane L tests first step q1 = L / 4 (a
                 // d - 1 neighbour) and second steps q2 = L % 4 and L % 4 + 4
                 // from there (d - 2 neighbours); the first valid q1 in
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
     k_trace(GridDev g, const uint32_t *__restrict__ starts, int n,
             const uint64_t *__restrict__ offsets, const int8_t *__restrict__ status,
             uint32_t *__restrict__ cells, uint32_t *__restrict__ ends, uint32_t *__restrict__ ends_d,
-            uint32_t *err, const uint32_t *__restrict__ order) {
+            uint32_t *err, const uint32_t *__restrict__ order, uint64_t skip_above = ~0ull) {
     constexpr int kW = TraceWin<DT>::side, kP = kW + 1, NWp = TraceWin<DT>::warps;
     __shared__ DT win[NWp][kW * kP];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -301,6 +306,7 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
         }
         return;
     }
+    if (CELLS && offsets[i + 1] - offsets[i] > skip_above) return;   // walked in segments
     const uint32_t c = starts[i];
     const uint32_t d0 = (uint32_t)reinterpret_cast<const DT *>(g.dist)[c];
     uint32_t e = 0;
@@ -309,6 +315,90 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
         ends[i] = e;
         if (ends_d) ends_d[i] = d0;
     }
+}
+
+// ---- long walks in segments ----
+
+// succ[c] = the next cell of the walk from c (the first neighbour in
+// tie-break order with distance d - 1), c itself for targets, unreached cells
+// and obstacles.
+template <typename DT>
+__global__ void k_succ(GridDev g, uint32_t *__restrict__ succ) {
+    const DT *dist = reinterpret_cast<const DT *>(g.dist);
+    const DT INF = (DT)~(DT)0;
+    const size_t n = (size_t)g.H * g.W;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const DT d = dist[c];
+        uint32_t nx = (uint32_t)c;
+        if (d != INF && d != (DT)0) {
+            const int y = (int)(c / (size_t)g.W), x = (int)(c % (size_t)g.W);
+            for (int q = 0; q < 8; ++q) {
+                const int yy = y + (int)((0xa940u >> (2 * q)) & 3u) - 1;
+                const int xx = x + (int)((0x9224u >> (2 * q)) & 3u) - 1;
+                if (yy < 0 || xx < 0 || yy >= g.H || xx >= g.W) continue;
+                const size_t o = (size_t)yy * g.W + xx;
+                if (dist[o] == (DT)(d - 1)) {
+                    nx = (uint32_t)o;
+                    break;
+                }
+            }
+        }
+        succ[c] = nx;
+    }
+}
+
+// out = in o in (one squaring of the jump table)
+__global__ void k_square(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, size_t n) {
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+        out[c] = in[in[c]];
+}
+
+// Thread per start: a walk longer than kLongWalk cells becomes segments of
+// kSegLen steps (the last one shorter); their first cells are kSegLen apart
+// along the walk, read from the jump table.
+template <typename DT>
+__global__ void k_segments(GridDev g, const uint32_t *__restrict__ starts, int n,
+                           const uint64_t *__restrict__ offsets, const int8_t *__restrict__ status,
+                           const uint32_t *__restrict__ jump, WalkSeg *__restrict__ segs, uint32_t cap,
+                           uint32_t *nseg, uint32_t *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || status[i] != MPN_PATH_OK) return;
+    const uint64_t o = offsets[i];
+    if (offsets[i + 1] - o <= kLongWalk) return;
+    const DT *dist = reinterpret_cast<const DT *>(g.dist);
+    uint32_t c = starts[i];
+    uint32_t d = (uint32_t)dist[c];
+    for (uint64_t k = 0;; ++k) {
+        const uint32_t dstop = d > kSegLen ? d - kSegLen : 0u;
+        const uint32_t idx = atomicAdd(nseg, 1u);
+        if (idx >= cap) {   // (the caller sizes the room; defensive)
+            atomicOr(err, ERR_TRACE);
+            return;
+        }
+        segs[idx] = WalkSeg{c, dstop, o + k * kSegLen};
+        if (dstop == 0u) return;
+        c = jump[c];
+        if ((uint32_t)dist[c] != dstop) {   // not a distance plane
+            atomicOr(err, ERR_TRACE);
+            return;
+        }
+        d = dstop;
+    }
+}
+
+// Warp per segment: the walk from its first cell down to its stop distance.
+template <typename DT>
+__global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
+    k_trace_segs(GridDev g, const WalkSeg *__restrict__ segs, const uint32_t *__restrict__ nseg,
+                 uint32_t *__restrict__ cells, uint32_t *err) {
+    constexpr int kW = TraceWin<DT>::side, kP = kW + 1, NWp = TraceWin<DT>::warps;
+    __shared__ DT win[NWp][kW * kP];
+    const int wl = threadIdx.x >> 5;
+    const uint32_t j = blockIdx.x * NWp + wl;
+    if (j >= *nseg) return;
+    const WalkSeg sg = segs[j];
+    uint32_t e = 0;
+    walk_path<DT, kW, true>(g, sg.cell, sg.out, win[wl], cells, err, &e, sg.dstop);
 }
 
 // ---- batched trace over the grids of a batch ----
@@ -523,8 +613,8 @@ cudaError_t launch_trace_lengths(const GridDev &g, int dist_bits, const uint32_t
                                  uint64_t *offsets, int8_t *status, Ctl *ctl, cudaStream_t st) {
     const int tb = 256, nb = (n + 1 + tb - 1) / tb;
     count_launch();
-    if (dist_bits == 16) k_lengths<uint16_t><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, &ctl->err);
-    else k_lengths<uint32_t><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, &ctl->err);
+    if (dist_bits == 16) k_lengths<uint16_t><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, &ctl->err, &ctl->walk_max);
+    else k_lengths<uint32_t><<<nb, tb, 0, st>>>(g, starts, n, offsets, status, &ctl->err, &ctl->walk_max);
     return cudaGetLastError();
 }
 
@@ -569,6 +659,54 @@ cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts
         count_launch();
         k_trace<uint32_t, true><<<(n + w - 1) / w, w * 32, 0, st>>>(g, starts, n, offsets, status, cells,
                                                                     nullptr, nullptr, err, ord);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_split(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                               const uint64_t *offsets, const int8_t *status, uint32_t *cells,
+                               uint32_t *order, uint32_t *jump, WalkSeg *segs, uint32_t seg_cap,
+                               uint32_t *nseg, cudaStream_t st, uint32_t *err) {
+    if (n <= 0) return cudaSuccess;
+    if (cudaError_t e = trace_attributes()) return e;
+    const size_t cells_n = (size_t)g.H * g.W;
+    uint32_t *a = jump, *b = jump + cells_n;
+    const int nb = grid_for(cells_n, 256);
+    cudaError_t e = cudaMemsetAsync(nseg, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    if (dist_bits == 16) k_succ<uint16_t><<<nb, 256, 0, st>>>(g, a);
+    else k_succ<uint32_t><<<nb, 256, 0, st>>>(g, a);
+    for (uint32_t m = 1; m < kSegLen; m *= 2) {   // a = succ^m -> succ^(2m)
+        count_launch();
+        k_square<<<nb, 256, 0, st>>>(a, b, cells_n);
+        uint32_t *t = a;
+        a = b;
+        b = t;
+    }
+    const int tb = 256;
+    count_launch(3);
+    if (dist_bits == 16)
+        k_segments<uint16_t><<<(n + tb - 1) / tb, tb, 0, st>>>(g, starts, n, offsets, status, a, segs, seg_cap, nseg, err);
+    else
+        k_segments<uint32_t><<<(n + tb - 1) / tb, tb, 0, st>>>(g, starts, n, offsets, status, a, segs, seg_cap, nseg, err);
+    // segments first (the longest work), then the walks that were not split
+    if (dist_bits == 16) {
+        constexpr int w = TraceWin<uint16_t>::warps;
+        k_trace_segs<uint16_t><<<(seg_cap + w - 1) / w, w * 32, 0, st>>>(g, segs, nseg, cells, err);
+        k_trace<uint16_t, true><<<(n + w - 1) / w, w * 32, 0, st>>>(g, starts, n, offsets, status, cells,
+                                                                    nullptr, nullptr, err, nullptr, kLongWalk);
+    } else {
+        constexpr int w = TraceWin<uint32_t>::warps;
+        k_trace_segs<uint32_t><<<(seg_cap + w - 1) / w, w * 32, 0, st>>>(g, segs, nseg, cells, err);
+        const uint32_t *ord = nullptr;
+        if (order) {
+            count_launch();
+            k_order<<<1, 1024, 0, st>>>(offsets, n, order);
+            ord = order;
+        }
+        k_trace<uint32_t, true><<<(n + w - 1) / w, w * 32, 0, st>>>(g, starts, n, offsets, status, cells,
+                                                                    nullptr, nullptr, err, ord, kLongWalk);
     }
     return cudaGetLastError();
 }

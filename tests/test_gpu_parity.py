@@ -411,6 +411,39 @@ def test_lookahead_on_and_off_equal_oracle(lookahead, monkeypatch):
                 assert np.array_equal(widen(pl.distances()), dL)
 
 
+def serpentine(H, W):
+    """Corridors along every other row, joined at alternating ends: the walk
+    from one end to the other is about H * W / 2 steps long."""
+    m = np.ones((H, W), np.uint8)
+    m[0::2, :] = 0
+    for r in range(1, H, 2):
+        m[r, W - 1 if (r // 2) % 2 == 0 else 0] = 0
+    return m
+
+
+@pytest.mark.parametrize("bits", [16, 32])
+def test_long_walks_split_into_segments_equal_oracle(bits):
+    """Walks longer than the split threshold are cut into segments found with
+    the jump table and walked side by side; with short walks, unreachable
+    starts and starts on obstacles in the same call, every path equals the
+    oracle's cell for cell (both dtypes)."""
+    m = serpentine(121, 401)
+    H, W = m.shape
+    free = np.flatnonzero(m.reshape(-1) == 0)
+    t = np.array([0], np.uint32)
+    rng = np.random.default_rng(5)
+    s = np.concatenate([[free[-1], free[-2], free[len(free) // 2], 1 * W + 3, free[5]],
+                        rng.choice(free, 40, replace=False)]).astype(np.uint32)
+    d, L = oracle.bfs(m, t)
+    assert L > 20000
+    with pkg.Planner(m, bits) as pl:
+        assert pl.propagate(t) == L
+        paths = pl.trace(s)
+    off, cells, status = oracle.trace(m, d, s)
+    assert np.array_equal(paths.status, status) and np.array_equal(paths.offsets, off)
+    assert np.array_equal(paths.cells, cells)
+
+
 def test_autotune_records_choice_and_stays_exact():
     m, t, s = rand_case(1500, 1400, 0.3, 6, 40, 77)
     with pkg.Planner(m) as pl:

@@ -245,6 +245,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
         uint32_t *list = p.lists + (size_t)(s % kListSlots) * MT;
         unsigned *work = &ctl->work[s % kListSlots];
         const uint32_t len = s_len;
+        // lookahead (and the done stamps it reads) only where the sweep has
+        // more than a quarter as many tiles as blocks: a tail of visits to fill
+        const bool la_s = p.lookahead && len > G / 4;
         int t = s_tile;
         if (t < 0 && threadIdx.x == 0) {
             const uint32_t i = pend_mine >= 0 ? (uint32_t)pend_mine : G + atomicAdd(work, 1u);
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             unsigned lastj;
             const MazeDesc *dp;
             int ty, tx;
-            const uint32_t l0 = visit(t, s, &fmask, &lastj, &slot, &dp, &ty, &tx, true);
+            const uint32_t l0 = visit(t, s, &fmask, &lastj, &slot, &dp, &ty, &tx, la_s);
             uint32_t pend_i = 0u;
             const bool pend_new = pend_gt >= 0 && pend_old < stamp;   // previous visit's push
             if (pend_new) pend_i = atomicAdd(&ctl->list_len[sl1], 1u);
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
                 s_tile = (next_i < len) ? take_entry_b(list, next_i) : -1;
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && la_s) {
                 s_done_t = t;   // published by the next visit's hook, or before the block waits
                 s_done_v = s + 1u;
             }
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->bar_count) : "memory");
         }
         const bool last = p.round_sweeps && s + 1 - s0 >= p.round_sweeps;   // the round's last sweep
-        const bool look = p.lookahead && !last;
+        const bool look = la_s && !last;
         uint32_t *list1 = p.lists + (size_t)sl1 * MT;
         const uint32_t *stamps0 = p.stamps + (size_t)(s % kStampSlots) * MT;
         bool fixed_taken = false;   // thread 0: this block's first entry of s + 1 ran

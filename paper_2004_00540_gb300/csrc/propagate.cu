@@ -177,6 +177,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     auto hook = [&]() {
         if (threadIdx.x == 32) publish_done();
     };
+    // Lookahead pays only where a sweep has enough tiles to leave a tail of
+    // visits to fill (more than a quarter as many as blocks, measured on the
+    // 23170^2 grid and the 1024^2 maze); a sparser sweep is about one round of
+    // visits side by side, so its visits publish no done stamps and its end
+    // has no lookahead. (Every block decides this from the same list length.)
+    bool la_s = false;
     // thread 0, after the visit's block barrier: its header (unless it logged
     // nothing: then the slot is reused); the tile's done stamp is due
     auto log_end_and_done = [&](int t, uint32_t l0v, uint32_t sweep) {
@@ -216,6 +222,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
         uint32_t *list = p.lists + (size_t)(s % kListSlots) * ntl;
         unsigned *work = &ctl->work[s % kListSlots];
         const uint32_t len = s_len;
+        la_s = p.lookahead && len > G / 4;
         // entries 0..G-1 go one per block without an atomic; the rest are
         // claimed with the counter (an index claimed while waiting at the last
         // barrier comes first)
@@ -250,7 +257,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             v.tx = t - v.ty * p.ntx;
             uint32_t fmask;
             unsigned lastj, jrun = 0;
-            wave::visit_tile<RXW, R, NW, WPL>(v, sm, &ctl->err, &fmask, &lastj, lg, &jrun, hook);
+            if (la_s) wave::visit_tile<RXW, R, NW, WPL>(v, sm, &ctl->err, &fmask, &lastj, lg, &jrun, hook);
+            else wave::visit_tile<RXW, R, NW, WPL>(v, sm, &ctl->err, &fmask, &lastj, lg, &jrun);
             uint32_t pend_i = 0u;
             const bool pend_new = pend_t >= 0 && pend_old < stamp;   // previous visit's push
             if (pend_new) pend_i = atomicAdd(&ctl->list_len[slot1], 1u);
@@ -262,7 +270,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                 s_tile = (next_i < len) ? take_entry(list, next_i) : -1;
             }
             __syncthreads();
-            if (threadIdx.x == 0) log_end_and_done(t, l0, s);
+            if (threadIdx.x == 0) {
+                log_end_and_done(t, l0, s);
+                if (!la_s) s_done_t = -1;   // no stamp needed
+            }
             if (threadIdx.x < 9) {
                 if (pend_new) wave::st_relaxed(p.lists + (size_t)slot1 * ntl + pend_i, (uint32_t)pend_t + 1u);
                 // this visit's push for border zone threadIdx.x: stamp now, append later
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
         }
         const uint32_t l1 = l0 + (uint32_t)p.k;          // layer at the start of sweep s + 1
         const bool more = !(p.max_layers && l1 >= p.max_layers) && s + 1 < p.sweep_cap;
-        const bool look = p.lookahead && more;
+        const bool look = la_s && more;
         uint32_t *list1 = p.lists + (size_t)slot1 * ntl;
         const uint32_t *stamps0 = p.stamps + (size_t)(s % kStampSlots) * ntl;
         bool fixed_taken = false;                          // thread 0: this block's first entry of s + 1 ran

@@ -624,6 +624,12 @@ struct mpn_batch {
     uint64_t *d_totals = nullptr, *h_totals = nullptr;
     uint32_t *d_walk_len = nullptr, *d_order = nullptr;
     size_t walk_cap = 0;
+    // walks longer than kLongWalk: a jump table (one grid at a time) and the
+    // segments of all of them (grown on demand, outside the arena budget)
+    uint32_t *d_jump = nullptr;
+    size_t jump_cells = 0;
+    BatchSeg *d_segs = nullptr;   // followed by the segment counter
+    size_t seg_cap = 0;
     std::map<uint64_t, cudaGraphExec_t> graphs;   // one captured round per (max_sweeps, lookahead)
     bool use_graph = true;
     float last_round_ms = 0.f;
@@ -727,8 +733,8 @@ mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_wjobs, b->max_slots * sizeof(WalkJob));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_wjobs, b->max_slots * sizeof(WalkJob));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_totals, b->max_slots * sizeof(uint64_t));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_totals, b->max_slots * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_totals, 2 * b->max_slots * sizeof(uint64_t));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_totals, 2 * b->max_slots * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) {
         mpn_batch_destroy(b);
@@ -993,12 +999,12 @@ static mpn_status finish_round(mpn_batch *b) {
         jb.dist_bits = m->dist_bits;
         jb.ns = (uint32_t)m->ns;
         jb.walk_base = base;
-        jb.pad = 0;
+        jb.split = 0;
         base += (uint32_t)m->ns;
     }
     B_TRY(cudaMemcpyAsync(b->d_wjobs, b->h_wjobs, nj * sizeof(WalkJob), cudaMemcpyHostToDevice, st));
     B_TRY(launch_batch_lengths(b->d_wjobs, nj, b->d_walk_len, b->d_totals, &ctl->err, st));
-    B_TRY(cudaMemcpyAsync(b->h_totals, b->d_totals, nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    B_TRY(cudaMemcpyAsync(b->h_totals, b->d_totals, 2 * nj * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     B_TRY(cudaStreamSynchronize(st));
     // the bit planes are not needed any more (walks read the distances);
     // paths of every finished grid whose paths fit in the arena now, walked
@@ -1019,11 +1025,55 @@ static mpn_status finish_round(mpn_batch *b) {
         m->paths_ready = true;
         any = any || m->total > 0;
     }
-    if (any) {
-        B_TRY(cudaMemcpyAsync(b->d_wjobs, b->h_wjobs, nj * sizeof(WalkJob), cudaMemcpyHostToDevice, st));
-        B_TRY(launch_batch_walks(b->d_wjobs, nj, b->d_walk_len, (uint32_t)nwalks, b->d_order, &ctl->err, st));
-        B_TRY(cudaStreamSynchronize(st));
+    if (!any) return MPN_OK;
+    // grids with walks far longer than the rest: those walks are cut into
+    // segments (first cells from a jump table), walked side by side
+    uint64_t segs_needed = 0;
+    size_t jump_need = 0;
+    for (int j = 0; j < nj; ++j) {
+        const HostMaze *m = done[j];
+        if (!b->h_wjobs[j].cells || b->h_totals[nj + j] <= kLongWalk) continue;
+        segs_needed += m->total / kSegLen + (uint64_t)m->ns + 1;
+        jump_need = std::max(jump_need, (size_t)m->H * m->W);
     }
+    bool split = segs_needed > 0 && segs_needed < 0xffffffffull;
+    if (split && jump_need > b->jump_cells) {
+        cudaFree(b->d_jump);
+        b->d_jump = nullptr;
+        b->jump_cells = 0;
+        if (cudaMalloc((void **)&b->d_jump, 2 * jump_need * sizeof(uint32_t)) == cudaSuccess) b->jump_cells = jump_need;
+        else cudaGetLastError();
+    }
+    if (split && segs_needed > b->seg_cap) {
+        cudaFree(b->d_segs);
+        b->d_segs = nullptr;
+        b->seg_cap = 0;
+        if (cudaMalloc((void **)&b->d_segs, segs_needed * sizeof(BatchSeg) + 16) == cudaSuccess) b->seg_cap = segs_needed;
+        else cudaGetLastError();
+    }
+    split = split && b->jump_cells >= jump_need && b->seg_cap >= segs_needed;   // else: walked whole
+    uint32_t *nseg = split ? (uint32_t *)(b->d_segs + b->seg_cap) : nullptr;
+    if (split)
+        for (int j = 0; j < nj; ++j)
+            if (b->h_wjobs[j].cells && b->h_totals[nj + j] > kLongWalk) b->h_wjobs[j].split = 1;
+    B_TRY(cudaMemcpyAsync(b->d_wjobs, b->h_wjobs, nj * sizeof(WalkJob), cudaMemcpyHostToDevice, st));
+    if (split) {
+        B_TRY(cudaMemsetAsync(nseg, 0, sizeof(uint32_t), st));
+        for (int j = 0; j < nj; ++j) {
+            const WalkJob &jb = b->h_wjobs[j];
+            if (!jb.split) continue;
+            uint32_t *table = nullptr;
+            B_TRY(launch_jump_table(jb.g, jb.dist_bits, b->d_jump, &table, st));
+            B_TRY(launch_batch_segments(b->d_wjobs, j, jb.ns, jb.dist_bits, table, b->d_segs,
+                                        (uint32_t)b->seg_cap, nseg, &ctl->err, st));
+        }
+        B_TRY(launch_batch_segwalks(b->d_wjobs, b->d_segs, nseg, (uint32_t)segs_needed, &ctl->err, st));
+    }
+    B_TRY(launch_batch_walks(b->d_wjobs, nj, b->d_walk_len, (uint32_t)nwalks, b->d_order, &ctl->err, st));
+    // a walk that found no cell one step closer (not a distance plane)
+    B_TRY(cudaMemcpyAsync(&b->h_bc->c.err, &ctl->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    B_TRY(cudaStreamSynchronize(st));
+    if (b->h_bc->c.err & ERR_TRACE) return MPN_ECUDA;
     return MPN_OK;
 }
 
@@ -1265,6 +1315,8 @@ void mpn_batch_destroy(mpn_batch *b) {
     cudaFree(b->d_totals);
     cudaFree(b->d_walk_len);
     cudaFree(b->d_order);
+    cudaFree(b->d_jump);
+    cudaFree(b->d_segs);
     if (b->h_wjobs) cudaFreeHost(b->h_wjobs);
     if (b->h_totals) cudaFreeHost(b->h_totals);
     delete b;

@@ -228,17 +228,34 @@ struct WalkJob {
     int dist_bits;
     uint32_t ns;
     uint32_t walk_base;         // index of this grid's first walk among all walks of the batch
-    uint32_t pad;
+    uint32_t split;             // 1: its walks longer than kLongWalk go in segments (not here)
 };
 // Per job: status and path length of every start, offsets (scan), the job's
-// path-cell total in totals[j], and every walk's length (saturated to 32
-// bits) in walk_len[walk_base + i].
+// path-cell total in totals[j] and its longest walk in totals[njobs + j], and
+// every walk's length (saturated to 32 bits) in walk_len[walk_base + i].
 cudaError_t launch_batch_lengths(const WalkJob *jobs, int njobs, uint32_t *walk_len,
                                  uint64_t *totals, uint32_t *err, cudaStream_t st);
 // The walks of every job with cells, longest first (order: nwalks words of
 // scratch).
 cudaError_t launch_batch_walks(const WalkJob *jobs, int njobs, const uint32_t *walk_len,
                                uint32_t nwalks, uint32_t *order, uint32_t *err, cudaStream_t st);
+// A segment of a long walk of batch job `job`.
+struct BatchSeg {
+    uint32_t cell, dstop, job, pad;
+    uint64_t out;
+};
+// The jump table succ^kSegLen of one grid in `jump` (2 * H * W words);
+// returns the half that holds it.
+cudaError_t launch_jump_table(const GridDev &g, int dist_bits, uint32_t *jump, uint32_t **table,
+                              cudaStream_t st);
+// Segments of the walks of job j (on the device) longer than kLongWalk, added
+// to segs (counter at nseg; room for cap).
+cudaError_t launch_batch_segments(const WalkJob *jobs, int j, uint32_t ns, int dist_bits,
+                                  const uint32_t *table, BatchSeg *segs, uint32_t cap, uint32_t *nseg,
+                                  uint32_t *err, cudaStream_t st);
+// Walk every segment (warp per segment; up to cap).
+cudaError_t launch_batch_segwalks(const WalkJob *jobs, const BatchSeg *segs, const uint32_t *nseg,
+                                  uint32_t cap, uint32_t *err, cudaStream_t st);
 cudaError_t launch_nearest(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
                            const int8_t *status, uint32_t *ends, uint32_t *ends_d, cudaStream_t st,
                            uint32_t *err);

@@ -408,6 +408,9 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
 __global__ void __launch_bounds__(256) k_lengths_batch(const WalkJob *__restrict__ jobs,
                                                        uint32_t *__restrict__ walk_len,
                                                        uint64_t *__restrict__ totals, uint32_t *err) {
+    __shared__ uint32_t s_max;
+    if (threadIdx.x == 0) s_max = 0u;
+    __syncthreads();
     const WalkJob jb = jobs[blockIdx.x];
     const GridDev &g = jb.g;
     const uint64_t N = (uint64_t)g.H * (uint64_t)g.W;
@@ -430,11 +433,16 @@ __global__ void __launch_bounds__(256) k_lengths_batch(const WalkJob *__restrict
         }
         jb.offsets[i + 1] = len;
         jb.status[i] = stt;
-        walk_len[jb.walk_base + i] = len > 0xffffffffull ? 0xffffffffu : (uint32_t)len;
+        const uint32_t l32 = len > 0xffffffffull ? 0xffffffffu : (uint32_t)len;
+        walk_len[jb.walk_base + i] = l32;
+        if (l32) atomicMax(&s_max, l32);
     }
     __syncthreads();
     block_scan_inplace(jb.offsets, (int)jb.ns);
-    if (threadIdx.x == 0) totals[blockIdx.x] = jb.offsets[jb.ns];
+    if (threadIdx.x == 0) {
+        totals[blockIdx.x] = jb.offsets[jb.ns];
+        totals[gridDim.x + blockIdx.x] = s_max;
+    }
 }
 
 // Walk order over flat lengths, longest first (as k_order).
@@ -458,13 +466,16 @@ __global__ void __launch_bounds__(1024) k_order_len(const uint32_t *__restrict__
 }
 
 // Warp per walk over every job: the walk's job is the last one whose first
-// walk index is not above it (jobs are in walk order). uint32 planes walk 64 x
-// 64 windows, uint16 planes 32 x 32 ones in the same buffer.
-constexpr int kBatchTraceWarps = 2;
+// walk index is not above it (jobs are in walk order). A batch's walks are
+// many (their total, not the longest one, sets the time), so they use 32 x 32
+// windows for both dtypes: four times as many walks fit on the GPU at once as
+// with the single-grid trace's 64 x 64 uint32 windows.
+constexpr int kBatchTraceWarps = 8;
+constexpr int kBatchWin = 32;
 __global__ void __launch_bounds__(kBatchTraceWarps * 32)
     k_trace_batch(const WalkJob *__restrict__ jobs, int njobs, const uint32_t *__restrict__ order,
                   uint32_t nwalks, uint32_t *err) {
-    __shared__ __align__(16) uint32_t win[kBatchTraceWarps][64 * 65];
+    __shared__ __align__(16) uint32_t win[kBatchTraceWarps][kBatchWin * (kBatchWin + 1)];
     const int wl = threadIdx.x >> 5;
     const uint32_t slot = blockIdx.x * kBatchTraceWarps + wl;
     if (slot >= nwalks) return;                 // whole warp leaves together
@@ -478,12 +489,62 @@ __global__ void __launch_bounds__(kBatchTraceWarps * 32)
     const WalkJob &jb = jobs[lo];
     const uint32_t i = w - jb.walk_base;
     if (i >= jb.ns || !jb.cells || jb.status[i] != MPN_PATH_OK) return;
+    if (jb.split && jb.offsets[i + 1] - jb.offsets[i] > kLongWalk) return;   // walked in segments
     uint32_t e = 0;
     if (jb.dist_bits == 16)
-        walk_path<uint16_t, 32, true>(jb.g, jb.starts[i], jb.offsets[i],
-                                      reinterpret_cast<uint16_t *>(win[wl]), jb.cells, err, &e);
+        walk_path<uint16_t, kBatchWin, true>(jb.g, jb.starts[i], jb.offsets[i],
+                                             reinterpret_cast<uint16_t *>(win[wl]), jb.cells, err, &e);
     else
-        walk_path<uint32_t, 64, true>(jb.g, jb.starts[i], jb.offsets[i], win[wl], jb.cells, err, &e);
+        walk_path<uint32_t, kBatchWin, true>(jb.g, jb.starts[i], jb.offsets[i], win[wl], jb.cells, err, &e);
+}
+
+// Thread per start of batch job j: its walk, if longer than kLongWalk cells,
+// becomes segments (as k_segments) tagged with the job.
+template <typename DT>
+__global__ void k_segments_batch(const WalkJob *__restrict__ jobs, int j, const uint32_t *__restrict__ jump,
+                                 BatchSeg *__restrict__ segs, uint32_t cap, uint32_t *nseg, uint32_t *err) {
+    const WalkJob &jb = jobs[j];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= jb.ns || jb.status[i] != MPN_PATH_OK) return;
+    const uint64_t o = jb.offsets[i];
+    if (jb.offsets[i + 1] - o <= kLongWalk) return;
+    const DT *dist = reinterpret_cast<const DT *>(jb.g.dist);
+    uint32_t c = jb.starts[i];
+    uint32_t d = (uint32_t)dist[c];
+    for (uint64_t k = 0;; ++k) {
+        const uint32_t dstop = d > kSegLen ? d - kSegLen : 0u;
+        const uint32_t idx = atomicAdd(nseg, 1u);
+        if (idx >= cap) {
+            atomicOr(err, ERR_TRACE);
+            return;
+        }
+        segs[idx] = BatchSeg{c, dstop, (uint32_t)j, 0u, o + k * kSegLen};
+        if (dstop == 0u) return;
+        c = jump[c];
+        if ((uint32_t)dist[c] != dstop) {
+            atomicOr(err, ERR_TRACE);
+            return;
+        }
+        d = dstop;
+    }
+}
+
+// Warp per segment of any job (32 x 32 windows, as k_trace_batch).
+__global__ void __launch_bounds__(kBatchTraceWarps * 32)
+    k_trace_segs_batch(const WalkJob *__restrict__ jobs, const BatchSeg *__restrict__ segs,
+                       const uint32_t *__restrict__ nseg, uint32_t *err) {
+    __shared__ __align__(16) uint32_t win[kBatchTraceWarps][kBatchWin * (kBatchWin + 1)];
+    const int wl = threadIdx.x >> 5;
+    const uint32_t q = blockIdx.x * kBatchTraceWarps + wl;
+    if (q >= *nseg) return;
+    const BatchSeg sg = segs[q];
+    const WalkJob &jb = jobs[sg.job];
+    uint32_t e = 0;
+    if (jb.dist_bits == 16)
+        walk_path<uint16_t, kBatchWin, true>(jb.g, sg.cell, sg.out, reinterpret_cast<uint16_t *>(win[wl]),
+                                             jb.cells, err, &e, sg.dstop);
+    else
+        walk_path<uint32_t, kBatchWin, true>(jb.g, sg.cell, sg.out, win[wl], jb.cells, err, &e, sg.dstop);
 }
 
 // Euclidean path reconstruction (Eq. 1 and the straightening rule after it),
@@ -663,17 +724,11 @@ cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts
     return cudaGetLastError();
 }
 
-cudaError_t launch_trace_split(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
-                               const uint64_t *offsets, const int8_t *status, uint32_t *cells,
-                               uint32_t *order, uint32_t *jump, WalkSeg *segs, uint32_t seg_cap,
-                               uint32_t *nseg, cudaStream_t st, uint32_t *err) {
-    if (n <= 0) return cudaSuccess;
-    if (cudaError_t e = trace_attributes()) return e;
+cudaError_t launch_jump_table(const GridDev &g, int dist_bits, uint32_t *jump, uint32_t **table,
+                              cudaStream_t st) {
     const size_t cells_n = (size_t)g.H * g.W;
     uint32_t *a = jump, *b = jump + cells_n;
     const int nb = grid_for(cells_n, 256);
-    cudaError_t e = cudaMemsetAsync(nseg, 0, sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
     count_launch();
     if (dist_bits == 16) k_succ<uint16_t><<<nb, 256, 0, st>>>(g, a);
     else k_succ<uint32_t><<<nb, 256, 0, st>>>(g, a);
@@ -684,6 +739,41 @@ cudaError_t launch_trace_split(const GridDev &g, int dist_bits, const uint32_t *
         a = b;
         b = t;
     }
+    *table = a;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_segments(const WalkJob *jobs, int j, uint32_t ns, int dist_bits,
+                                  const uint32_t *table, BatchSeg *segs, uint32_t cap, uint32_t *nseg,
+                                  uint32_t *err, cudaStream_t st) {
+    if (ns == 0) return cudaSuccess;
+    count_launch();
+    if (dist_bits == 16)
+        k_segments_batch<uint16_t><<<(ns + 255) / 256, 256, 0, st>>>(jobs, j, table, segs, cap, nseg, err);
+    else
+        k_segments_batch<uint32_t><<<(ns + 255) / 256, 256, 0, st>>>(jobs, j, table, segs, cap, nseg, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_segwalks(const WalkJob *jobs, const BatchSeg *segs, const uint32_t *nseg,
+                                  uint32_t cap, uint32_t *err, cudaStream_t st) {
+    if (cap == 0) return cudaSuccess;
+    count_launch();
+    k_trace_segs_batch<<<(cap + kBatchTraceWarps - 1) / kBatchTraceWarps, kBatchTraceWarps * 32, 0, st>>>(
+        jobs, segs, nseg, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_split(const GridDev &g, int dist_bits, const uint32_t *starts, int n,
+                               const uint64_t *offsets, const int8_t *status, uint32_t *cells,
+                               uint32_t *order, uint32_t *jump, WalkSeg *segs, uint32_t seg_cap,
+                               uint32_t *nseg, cudaStream_t st, uint32_t *err) {
+    if (n <= 0) return cudaSuccess;
+    if (cudaError_t e = trace_attributes()) return e;
+    cudaError_t e = cudaMemsetAsync(nseg, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    uint32_t *a = nullptr;
+    if ((e = launch_jump_table(g, dist_bits, jump, &a, st)) != cudaSuccess) return e;
     const int tb = 256;
     count_launch(3);
     if (dist_bits == 16)
@@ -771,6 +861,10 @@ cudaError_t launch_batch_walks(const WalkJob *jobs, int njobs, const uint32_t *w
     std::call_once(once, [] {
         ea = cudaFuncSetAttribute((const void *)k_trace_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
                                   cudaSharedmemCarveoutMaxShared);
+        if (ea == cudaSuccess)
+            ea = cudaFuncSetAttribute((const void *)k_trace_segs_batch,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared);
     });
     if (ea != cudaSuccess) return ea;
     count_launch(2);

@@ -181,3 +181,27 @@ def test_batch_without_lookahead_same_results(monkeypatch):
         b.run(0)
         for tk, w in zip(tks, ws):
             check(b, tk, w)
+
+
+def test_batch_long_walks_in_segments():
+    """Grids whose walks are far longer than the rest (serpentine corridors,
+    both dtypes) in one batch with ordinary grids: their long walks go in
+    segments found with a jump table; every path equals the oracle's."""
+    def serp(H, W):
+        m = np.ones((H, W), np.uint8)
+        m[0::2, :] = 0
+        for r in range(1, H, 2):
+            m[r, W - 1 if (r // 2) % 2 == 0 else 0] = 0
+        return m
+    ws = small_members(6, side_hi=300, base_seed=170)
+    extra = []
+    for H, W, bits in ((121, 401, 16), (161, 511, 32)):
+        m = serp(H, W)
+        free = np.flatnonzero(m.reshape(-1) == 0)
+        st = np.concatenate([[free[-1], free[len(free) // 3], 3], free[::997]]).astype(np.uint32)
+        extra.append(synth.Workload(f"serp{H}x{W}", m, np.array([0], np.uint32), st, bits, {}))
+    with pkg.Batch(1 << 30) as b:
+        tks = [(b.submit(w.mask, w.targets, w.starts, w.dist_bits), w) for w in ws + extra]
+        b.run(0)
+        for tk, w in tks:
+            check(b, tk, w)

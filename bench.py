@@ -331,6 +331,30 @@ def run_per_config(pkg, torch, reps: int = 5):
     return out
 
 
+def autotune_buckets(ws, dev, pkg):
+    """Before the batched leg (outside its timed region): the autotuner on one
+    grid per size bucket ceil(log2(side)) -- the smallest DFS maze of the
+    bucket, the kind whose many layers set the batch's time -- so that the
+    batch takes each bucket's measured depth for its tile shape (shape 0)."""
+    pick = {}
+    for i, w in enumerate(ws):
+        b = int(np.ceil(np.log2(max(w.H, w.W))))
+        if i % 2 == 1 and (b not in pick or w.H * w.W < ws[pick[b]].H * ws[pick[b]].W):
+            pick[b] = i
+    tuned = {}
+    for b in sorted(pick):
+        i = pick[b]
+        w = ws[i]
+        m, t, _ = dev[i]
+        with pkg.Planner(m, w.dist_bits) as pl:
+            v, d, ms = pl.autotune(t)
+        q = pkg.mpn_tune_query(w.H, w.W, 0)
+        tuned[str(b)] = {"grid": w.name, "side": w.H, "best_variant": v, "best_depth": d,
+                         "best_ms": ms, "batch_shape0_depth": q[0] if q else None,
+                         "batch_shape0_ms": q[1] if q else None}
+    return tuned
+
+
 def run_batched(args, pkg, torch):
     """The 256-maze stream: batched capacity, per-maze baselines, serving."""
     from paper_2004_00540_gb300.serve import Request, serve
@@ -342,6 +366,7 @@ def run_batched(args, pkg, torch):
     budget = int(sum(w.H * w.W * 5 + 4096 * 64 for w in ws) * 1.5) + (256 << 20)
     out = {"workload": f"{len(ws)} grids, side U{{64..2048}}, even Bernoulli(0.3) / odd DFS maze, "
                        f"1-16 targets, 10-200 starts", "cells": int(cells)}
+    out["tuned"] = autotune_buckets(ws, dev, pkg)
 
     # page-locked host buffers for every grid's paths, allocated once and
     # sized by the warm-up run (as a serving process keeps its response

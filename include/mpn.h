@@ -248,6 +248,13 @@ mpn_status mpn_set_tuning(mpn_ctx *ctx, int32_t variant, int32_t depth);
 mpn_status mpn_autotune(mpn_ctx *ctx, const uint32_t *targets, int32_t n_targets,
                         int32_t *variant, int32_t *depth, float *best_ms);
 
+/* What the autotuner recorded for the size bucket of an H x W grid
+ * (ceil(log2(max(H, W)))) and tile shape `variant`: the fastest depth and its
+ * propagation time in ms (either output may be NULL). Batches use that depth
+ * for grids of this bucket. MPN_ESTATE if nothing was measured for it,
+ * MPN_EINVAL for sizes < 1 or an unknown shape. No counterpart in the paper. */
+mpn_status mpn_tune_query(int32_t H, int32_t W, int32_t variant, int32_t *depth, float *ms);
+
 /* Shape of compiled tile variant v: region rows, region words (32 cells
  * each), threads per block. MPN_EINVAL past the last variant. No counterpart
  * in the paper. */

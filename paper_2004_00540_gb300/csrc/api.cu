@@ -833,6 +833,16 @@ mpn_status mpn_nearest_targets(mpn_ctx *c, const uint32_t *starts, int32_t n, ui
     return MPN_OK;
 }
 
+mpn_status mpn_tune_query(int32_t H, int32_t W, int32_t variant, int32_t *depth, float *ms) {
+    if (H < 1 || W < 1 || variant < 0 || variant >= num_variants()) return MPN_EINVAL;
+    std::lock_guard<std::mutex> lk(g_tune.mu);
+    const int b = bucket_of(H, W);
+    if (!g_tune.depth[b][variant]) return MPN_ESTATE;
+    if (depth) *depth = g_tune.depth[b][variant];
+    if (ms) *ms = g_tune.ms[b][variant];
+    return MPN_OK;
+}
+
 mpn_status mpn_autotune(mpn_ctx *c, const uint32_t *targets, int32_t n, int32_t *variant,
                         int32_t *depth, float *best_ms) {
     if (!c || !targets || n < 1) return MPN_EINVAL;

@@ -31,7 +31,7 @@ EXPORTS = (
     "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_submit", "mpn_batch_run",
     "mpn_batch_poll", "mpn_batch_wait", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
     "mpn_batch_stats", "mpn_batch_destroy", "mpn_autotune", "mpn_trace_euclid",
-    "mpn_nearest_targets", "mpn_last_error",
+    "mpn_nearest_targets", "mpn_last_error", "mpn_tune_query",
 )
 MPN_BATCH_PENDING, MPN_BATCH_DONE, MPN_BATCH_FAILED = 0, 1, 2
 
@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
                                  ctypes.c_int),
             "mpn_get_stats": ([vp, ctypes.POINTER(mpn_stats)], ctypes.c_int),
             "mpn_launch_count": ([], u64),
+            "mpn_tune_query": ([i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)],
+                               ctypes.c_int),
             "mpn_propagate_noalloc": ([vp, i32, i32, vp, i32, u32, vp, vp], ctypes.c_int),
             "mpn_batch_create": ([u64, i32, vp, pp], ctypes.c_int),
             "mpn_batch_set_depth": ([vp, i32], ctypes.c_int),
@@ -313,6 +315,17 @@ def mpn_autotune(ctx, targets):
     _check(load().mpn_autotune(ctx, _ptr(targets)[0], n, ctypes.byref(v), ctypes.byref(d),
                                ctypes.byref(ms)), "mpn_autotune")
     return v.value, d.value, ms.value
+
+
+def mpn_tune_query(H: int, W: int, variant: int):
+    """(depth, ms) the autotuner recorded for this size bucket and tile shape,
+    or None if nothing was measured for it."""
+    d, ms = ctypes.c_int32(), ctypes.c_float()
+    st = load().mpn_tune_query(H, W, variant, ctypes.byref(d), ctypes.byref(ms))
+    if st == MPN_ESTATE:
+        return None
+    _check(st, "mpn_tune_query")
+    return d.value, ms.value
 
 
 def mpn_launch_count() -> int:

@@ -51,3 +51,14 @@ def test_argument_errors_need_no_gpu():
     assert L.mpn_get_distances_async(None, buf, None) == pkg.MPN_EINVAL
     assert L.mpn_trace(None, None, 0, None, None, 0, None) == pkg.MPN_EINVAL
     assert L.mpn_launch_count() == 0
+
+
+def test_tune_query_without_gpu():
+    """The autotuner's table is host memory: nothing recorded yet for a size
+    bucket means None; bad sizes and shapes are argument errors."""
+    import paper_2004_00540_gb300 as pkg
+    assert pkg.mpn_tune_query(3, 5, 0) is None
+    with pytest.raises(pkg.MPNError):
+        pkg.mpn_tune_query(0, 5, 0)
+    with pytest.raises(pkg.MPNError):
+        pkg.mpn_tune_query(64, 64, 999)

@@ -118,6 +118,26 @@ mpn_status mpn_propagate(mpn_ctx *ctx, const uint32_t *targets, int32_t n_target
                          uint32_t max_layers, uint32_t *layers_run);
 
 /*
+ * Continue the wave from a given distance plane (the paper's recursive mode,
+ * Appendix, Table I, which feeds the activity map of one network run into the
+ * next: here that map is given as distances, d = L + 1 - O; Methods,
+ * "Activity Map Generation"). dist_in: H*W elements of the context's dtype,
+ * host or device; a cell with distance <= from_layer is reached at that
+ * distance (it must be free, else MPN_EINVAL from the GPU); every other cell
+ * starts unreached, whatever dist_in holds there. Layers from_layer + 1 ..
+ * max_layers run (max_layers = 0: until a layer adds nothing; else it must be
+ * > from_layer), and the context's distance plane gets the result: the kept
+ * cells, then every cell reached by those layers at its first layer.
+ * layers_run (may be NULL): the largest distance reached by those layers, 0
+ * if none; passing it makes the call wait and report errors. This is how a
+ * grid split into row strips over several GPUs advances: each strip runs k
+ * layers from the plane it and its neighbours agree on, then they exchange
+ * k-row halos.
+ */
+mpn_status mpn_propagate_resume(mpn_ctx *ctx, const void *dist_in, uint32_t from_layer,
+                                uint32_t max_layers, uint32_t *layers_run);
+
+/*
  * Same result as mpn_propagate, computed the way the paper's recursive mode
  * runs (Appendix, Table I: one layer per iteration): one kernel launch per
  * layer over the whole distance plane, with the host reading a "did anything

@@ -509,9 +509,11 @@ mpn_status mpn_variant_info(int32_t v, int32_t *rows, int32_t *words, int32_t *t
     return MPN_OK;
 }
 
-mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_t max_layers,
-                         uint32_t *layers_run) {
-    if (!c || !targets || n < 1) return MPN_EINVAL;
+// A run of the persistent kernel (and the log decode) seeded either from
+// targets (din null: layer 0 = the targets) or from a distance plane din
+// (device, H * W of the dtype; cells at distance <= from are kept).
+static mpn_status run_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, const void *din,
+                                uint32_t from, uint32_t max_layers, uint32_t *layers_run) {
     // activation log: room for 1.5 entries per plane word plus one partly
     // filled chunk per block (a block that finds it full writes distances
     // itself, so the size only affects speed). The TMA-staged variant writes
@@ -535,7 +537,7 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
         log_chunks = 0;
     }
     const uint32_t *dt = nullptr;
-    mpn_status st = begin_propagate(c, targets, n, &dt, log_chunks == 0);
+    mpn_status st = din ? MPN_OK : begin_propagate(c, targets, n, &dt, log_chunks == 0);
     if (st != MPN_OK) return st;
     const size_t ntiles = (size_t)c->ntx * c->nty;
     PropParams p{};
@@ -551,13 +553,14 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
     p.TY = c->TY;
     p.TXW = c->TXW;
     p.max_layers = max_layers;
+    p.l_base = from;
     p.spin_limit = kSpinLimit;
     p.lookahead = 1;
     // (test hook: MPN_TEST_NO_LOOKAHEAD=1 makes blocks only wait at a sweep's end)
     if (const char *e = getenv("MPN_TEST_NO_LOOKAHEAD")) p.lookahead = (e[0] == '1') ? 0u : 1u;
     p.log = log_chunks ? (uint32_t *)c->log.p : nullptr;
     p.log_chunks = log_chunks;
-    const uint64_t bound = (max_layers ? (uint64_t)max_layers : (uint64_t)c->H * c->W) / c->depth + 3;
+    const uint64_t bound = (max_layers ? (uint64_t)(max_layers - from) : (uint64_t)c->H * c->W) / c->depth + 3;
     p.sweep_cap = (uint32_t)(bound < (1u << 22) ? bound : (1u << 22));
     // test hooks that make the device-side limits run out on purpose (the
     // kernel then records the error and every block returns):
@@ -570,7 +573,8 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
         const long v = strtol(e, nullptr, 10);
         if (v >= 1 && (uint64_t)v < p.sweep_cap) p.sweep_cap = (uint32_t)v;
     }
-    MPN_TRY(launch_seed(dt, n, p, c->dist_bits, c->stream));
+    if (din) MPN_TRY(launch_seed_plane(din, p, c->dist_bits, c->stream));
+    else MPN_TRY(launch_seed(dt, n, p, c->dist_bits, c->stream));
     MPN_TRY(cudaEventRecord(c->ev[2], c->stream));   // times the persistent kernel + log decode
     MPN_TRY(launch_propagate(c->variant, c->dist_bits, p, c->blocks, c->stream));
     MPN_TRY(launch_log_decode(p, c->dist_bits, c->sm_count, slots, c->stream));
@@ -585,6 +589,37 @@ mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_
         *layers_run = c->last_layers;
     }
     return MPN_OK;
+}
+
+mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_t max_layers,
+                         uint32_t *layers_run) {
+    if (!c || !targets || n < 1) return MPN_EINVAL;
+    return run_propagate(c, targets, n, nullptr, 0u, max_layers, layers_run);
+}
+
+mpn_status mpn_propagate_resume(mpn_ctx *c, const void *dist_in, uint32_t from_layer,
+                                uint32_t max_layers, uint32_t *layers_run) {
+    if (!c || !dist_in) return MPN_EINVAL;
+    if (max_layers && max_layers <= from_layer) return MPN_EINVAL;
+    const uint32_t inf = c->dist_bits == 16 ? 0xffffu : 0xffffffffu;
+    if (from_layer >= inf) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);   // drain an earlier run's error report
+    (void)st;
+    if (c->out_pending) {   // the plane is rewritten below: after the pending copy
+        MPN_TRY(cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+        c->out_pending = false;
+    }
+    c->propagated = false;
+    // the seed reads the plane and writes the context's own plane (in place
+    // for a host plane, which goes there first)
+    const void *din = dist_in;
+    if (!is_device_ptr(dist_in)) {
+        MPN_TRY(cudaMemcpyAsync(c->dist.p, dist_in, c->dist_bytes(), cudaMemcpyHostToDevice, c->stream));
+        din = c->dist.p;
+    }
+    MPN_TRY(cudaMemsetAsync(c->state.p, 0, c->plane_words() * 16, c->stream));
+    MPN_TRY(cudaMemsetAsync(c->ctl.p, 0, sizeof(Ctl), c->stream));
+    return run_propagate(c, nullptr, 0, din, from_layer, max_layers, layers_run);
 }
 
 mpn_status mpn_propagate_plain(mpn_ctx *c, const uint32_t *targets, int32_t n,

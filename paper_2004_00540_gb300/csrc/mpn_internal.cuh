@@ -83,7 +83,8 @@ struct PropParams {
     int k;                       // temporal depth (layers per sweep), halo rows
     int TY;                      // interior rows per tile
     int TXW;                     // interior words per tile
-    uint32_t max_layers;         // 0 = until nothing changes
+    uint32_t max_layers;         // 0 = until nothing changes; else the last layer (absolute)
+    uint32_t l_base;             // layer the run starts from: sweep s covers l_base + s k + 1 ..
     uint32_t spin_limit;         // barrier wait limit (iterations of ~100 ns)
     uint32_t lookahead;          // 1: blocks waiting at a sweep's end run ready tiles of the next
     uint32_t sweep_cap;          // more sweeps than this is an error
@@ -173,6 +174,11 @@ cudaError_t launch_log_decode(const PropParams &p, int dist_bits, int sm_count, 
                               cudaStream_t st);
 cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int dist_bits,
                         cudaStream_t st);
+// Seed a run that resumes from a distance plane: cells at distance <= from
+// (= p.l_base) are reached and keep their distance, all others start
+// unreached; tiles with cells at distance `from` are queued for sweep 0. din
+// (H * W of the dtype, device) may be the context's own plane.
+cudaError_t launch_seed_plane(const void *din, const PropParams &p, int dist_bits, cudaStream_t st);
 cudaError_t launch_plain_layer(const GridDev &g, int dist_bits, uint32_t layer, Ctl *ctl,
                                cudaStream_t st);
 cudaError_t launch_plain_seed(const uint32_t *targets, int n, const GridDev &g, int dist_bits,

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     };
 
     for (uint32_t s = 0;; ++s) {
-        const uint32_t l0 = s * (uint32_t)p.k;
+        const uint32_t l0 = p.l_base + s * (uint32_t)p.k;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             // list slot (s + 3) % 4 last served sweep s - 1 (no block claims
             // from it any more) and next serves sweep s + 3
@@ -773,7 +773,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
     v.k = p.k;
     const size_t ntl = (size_t)ntiles;
     for (uint32_t s = 0;; ++s) {
-        const uint32_t l0 = s * (uint32_t)p.k;
+        const uint32_t l0 = p.l_base + s * (uint32_t)p.k;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ctl->work[(s + 3) % kListSlots] = 0u;
             ctl->list_len[(s + 3) % kListSlots] = 0u;
@@ -933,6 +933,41 @@ __global__ void k_seed(const uint32_t *targets, int n, PropParams p) {
         const int ty = y / p.TY, tx = (x >> 5) / p.TXW;
         const int ri = y - ty * p.TY, wi = (x >> 5) - tx * p.TXW;
         push_reached(p, ty, tx, border_bits(ri, wi, bit, p.k, p.TY, p.TXW), 0u);
+    }
+}
+
+// Seed from a distance plane (a run that resumes): warp per plane word, lane
+// = cell. A cell at distance <= from is reached and keeps its distance (an
+// obstacle marked reached is ERR_INVAL); every other cell starts unreached.
+// Tiles holding cells at distance `from` are queued for sweep 0 with the
+// border zones those frontier cells touch.
+template <typename DT>
+__global__ void k_seed_plane(const DT *__restrict__ din, PropParams p) {
+    const GridDev &g = p.g;
+    const size_t wid = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (wid >= (size_t)g.H * g.P) return;   // whole warp leaves together
+    const int y = (int)(wid / (size_t)g.P), w = (int)(wid % (size_t)g.P);
+    const int x = 32 * w + lane;
+    const DT INF = (DT)~(DT)0;
+    const uint32_t from = p.l_base;
+    DT d = INF;
+    if (x < g.W) d = din[(size_t)y * g.W + x];
+    const bool reached = x < g.W && d != INF && (uint32_t)d <= from;
+    const unsigned vb = __ballot_sync(0xffffffffu, reached);
+    const unsigned fb = __ballot_sync(0xffffffffu, reached && (uint32_t)d == from);
+    if (x < g.W) reinterpret_cast<DT *>(g.dist)[(size_t)y * g.W + x] = reached ? d : INF;
+    if (lane == 0) {
+        const size_t wo = (size_t)y * g.P + w;
+        if (vb & ~g.free_bits[wo]) atomicOr(&p.ctl->err, ERR_INVAL);
+        const uint32_t v = vb & g.free_bits[wo];
+        wave::st_pair(g.state + 4 * wo, v, 0u);
+        wave::st_pair(g.state + 4 * wo + 2, v, 0u);
+        const uint32_t f = fb & v;
+        if (f && w < p.ntx * p.TXW) {
+            const int ty = y / p.TY, tx = w / p.TXW;
+            push_reached(p, ty, tx, border_bits(y - ty * p.TY, w - tx * p.TXW, f, p.k, p.TY, p.TXW), 0u);
+        }
     }
 }
 
@@ -1136,6 +1171,16 @@ cudaError_t launch_seed(const uint32_t *targets, int n, const PropParams &p, int
     count_launch();
     if (dist_bits == 16) k_seed<uint16_t><<<nb, tb, 0, st>>>(targets, n, p);
     else k_seed<uint32_t><<<nb, tb, 0, st>>>(targets, n, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_plane(const void *din, const PropParams &p, int dist_bits, cudaStream_t st) {
+    const size_t words = (size_t)p.g.H * p.g.P;
+    const int wpb = 8;
+    const size_t nb = (words + wpb - 1) / wpb;
+    count_launch();
+    if (dist_bits == 16) k_seed_plane<uint16_t><<<(unsigned)nb, wpb * 32, 0, st>>>((const uint16_t *)din, p);
+    else k_seed_plane<uint32_t><<<(unsigned)nb, wpb * 32, 0, st>>>((const uint32_t *)din, p);
     return cudaGetLastError();
 }
 

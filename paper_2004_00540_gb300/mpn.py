@@ -31,7 +31,7 @@ EXPORTS = (
     "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_submit", "mpn_batch_run",
     "mpn_batch_poll", "mpn_batch_wait", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
     "mpn_batch_stats", "mpn_batch_destroy", "mpn_autotune", "mpn_trace_euclid",
-    "mpn_nearest_targets", "mpn_last_error", "mpn_tune_query",
+    "mpn_nearest_targets", "mpn_last_error", "mpn_tune_query", "mpn_propagate_resume",
 )
 MPN_BATCH_PENDING, MPN_BATCH_DONE, MPN_BATCH_FAILED = 0, 1, 2
 
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
             "mpn_set_stream": ([vp, vp], ctypes.c_int),
             "mpn_propagate": ([vp, vp, i32, u32, ctypes.POINTER(u32)], ctypes.c_int),
             "mpn_propagate_plain": ([vp, vp, i32, u32, i32, ctypes.POINTER(u32)], ctypes.c_int),
+            "mpn_propagate_resume": ([vp, vp, u32, u32, ctypes.POINTER(u32)], ctypes.c_int),
             "mpn_get_distances": ([vp, vp, i32], ctypes.c_int),
             "mpn_get_distances_async": ([vp, vp, vp], ctypes.c_int),
             "mpn_get_activity": ([vp, u32, vp, i32], ctypes.c_int),
@@ -212,6 +213,19 @@ def mpn_propagate(ctx, targets, max_layers: int = 0, wait: bool = True):
         _check(load().mpn_propagate(ctx, p, n, max_layers, ctypes.byref(lr)), "mpn_propagate")
         return int(lr.value)
     _check(load().mpn_propagate(ctx, p, n, max_layers, None), "mpn_propagate")
+    return None
+
+
+def mpn_propagate_resume(ctx, dist_in, from_layer: int, max_layers: int = 0, wait: bool = True):
+    """Continue from a distance plane (cells <= from_layer kept); returns the
+    largest distance the new layers reached (0 if none) when wait."""
+    p, _ = _ptr(dist_in)
+    if wait:
+        lr = ctypes.c_uint32(0)
+        _check(load().mpn_propagate_resume(ctx, p, from_layer, max_layers, ctypes.byref(lr)),
+               "mpn_propagate_resume")
+        return int(lr.value)
+    _check(load().mpn_propagate_resume(ctx, p, from_layer, max_layers, None), "mpn_propagate_resume")
     return None
 
 

@@ -447,6 +447,46 @@ def run_batched(args, pkg, torch):
     return out
 
 
+def run_batched_sharded(args, pkg, torch, rank, world, pg):
+    """The 256-grid stream over `world` ranks: rank r solves grids r, r + world,
+    ... in its own batch (independent problems, no collective on the data
+    path); whole-job grids/s = all grids / the slowest rank's time."""
+    ws = synth.c4_batch(args.batch_n)
+    mine = shard(len(ws), rank, world)
+    sub = [ws[i] for i in mine]
+    dev = [(torch.from_numpy(w.mask).cuda(), torch.from_numpy(w.targets.view(np.int32)).cuda(),
+            torch.from_numpy(w.starts.view(np.int32)).cuda()) for w in sub]
+    budget = int(sum(w.H * w.W * 5 + 4096 * 64 for w in sub) * 1.5) + (256 << 20)
+
+    def once(host=None):
+        with pkg.Batch(budget) as b:
+            tks = [b.submit(m, t, s, w.dist_bits) for (m, t, s), w in zip(dev, sub)]
+            b.run(0)
+            tot = [b.info(tk)["total_cells"] for tk in tks]
+            if host is not None:
+                a = 0
+                for tk, w, x in zip(tks, sub, tot):
+                    b.result(tk, w.starts.size, want_dist=False, cells=host[0][a:a + max(x, 1)],
+                             offsets=host[1][:w.starts.size + 1], status=host[2][:max(w.starts.size, 1)])
+                    a += max(x, 1)
+        return tot
+
+    tot = once()
+    host = (torch.empty(sum(max(x, 1) for x in tot), dtype=torch.int32).pin_memory(),
+            torch.empty(max(w.starts.size for w in sub) + 1, dtype=torch.int64).pin_memory(),
+            torch.empty(max(w.starts.size for w in sub) + 1, dtype=torch.int8).pin_memory())
+    pg.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    once(host)
+    torch.cuda.synchronize()
+    local_ms = (time.perf_counter() - t0) * 1e3
+    t_ms, rate = aggregate(local_ms, len(ws) / world, 1, world, pg, "cuda")
+    return {"workload": f"{len(ws)} grids, side U{{64..2048}}, sharded round-robin over {world} ranks",
+            "mazes_per_s": rate, "seconds": t_ms * 1e-3, "grids_this_rank": len(sub),
+            "scaling": "weak (grids per rank fixed by the shard)"}
+
+
 PAPER_FIG5_S_PER_L_N2 = 3.0751e-10   # seconds per layer per cell, GTX 1080 Ti (Results, run-time)
 
 
@@ -709,6 +749,9 @@ def main():
                        "at a time, nothing overlapped"}
 
     pkg.mpn_destroy(ctx)
+    sharded = None
+    if world > 1 and not args.no_batched:
+        sharded = run_batched_sharded(args, pkg, torch, rank, world, pg)
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -738,6 +781,8 @@ def main():
         pg.destroy_process_group()
     if not args.no_batched and world == 1:
         line["batched"] = run_batched(args, pkg, torch)
+    if sharded is not None:
+        line["batched"] = {"sharded": sharded}
     if not args.no_per_config and world == 1:
         line["per_config"] = run_per_config(pkg, torch)
     if not args.no_cpu and world == 1:

@@ -54,7 +54,8 @@ typedef enum {
     MPN_ETIMEOUT = 4,   /* a grid-wide wait ran past its iteration limit */
     MPN_EOVERFLOW = 5,  /* a distance does not fit the uint16 plane */
     MPN_EOBSTACLE = 6,  /* a target lies on an obstacle */
-    MPN_ESTATE = 7      /* call out of order (trace before propagate) */
+    MPN_ESTATE = 7,     /* call out of order (trace before propagate) */
+    MPN_ECHECK = 8      /* the on-device invariant check found violations (mpn_check) */
 } mpn_status;
 
 /* distance plane element type */
@@ -118,10 +119,12 @@ mpn_status mpn_propagate(mpn_ctx *ctx, const uint32_t *targets, int32_t n_target
                          uint32_t max_layers, uint32_t *layers_run);
 
 /*
- * Continue the wave from a given distance plane (the paper's recursive mode,
- * Appendix, Table I, which feeds the activity map of one network run into the
- * next: here that map is given as distances, d = L + 1 - O; Methods,
- * "Activity Map Generation"). dist_in: H*W elements of the context's dtype,
+ * Continue the wave from a given distance plane: one more batch of layers,
+ * with the activity of the last one passed back to its start (Results,
+ * "Limitations and Practical Considerations": i iterations of up to L_max
+ * layers when L is larger; and the recursive mode of Appendix, Table I). The
+ * map is given as distances, d = L + 1 - O (Methods, "Activity Map
+ * Generation"). dist_in: H*W elements of the context's dtype,
  * host or device; a cell with distance <= from_layer is reached at that
  * distance (it must be free, else MPN_EINVAL from the GPU); every other cell
  * starts unreached, whatever dist_in holds there. Layers from_layer + 1 ..
@@ -231,6 +234,22 @@ mpn_status mpn_trace_euclid(mpn_ctx *ctx, const uint32_t *starts, int32_t n, uin
  */
 mpn_status mpn_nearest_targets(mpn_ctx *ctx, const uint32_t *starts, int32_t n,
                                uint32_t *target, uint32_t *dist);
+
+/*
+ * On-device check of the last propagation's distance plane against what a
+ * multi-source, 8-connected, unit-cost distance map must satisfy (Methods,
+ * "Activity Map Generation": a cell first activates one layer after its most
+ * active neighbour): every reached cell other than a target has a neighbour at
+ * distance d - 1; two reached neighbours differ by at most 1; a free
+ * neighbour of a reached cell is reached, unless the fixed depth (max_layers)
+ * stopped the wave there; obstacles are unreached. *violations (may be NULL):
+ * cells that break one of these. Returns MPN_ECHECK if there are any, else
+ * MPN_OK; waits for the GPU. MPN_ESTATE before the first propagate. With the
+ * environment variable MPN_CHECK=1, every mpn_propagate that waits
+ * (layers_run non-NULL) runs this check too and returns MPN_ECHECK on a
+ * violation (a debug mode; it reads the whole plane once more).
+ */
+mpn_status mpn_check(mpn_ctx *ctx, uint64_t *violations);
 
 /* Wait for the context's stream and for its pending asynchronous distance
  * copy (mpn_get_distances_async); report any error the GPU recorded. No

@@ -143,6 +143,7 @@ struct mpn_ctx {
     DevBuf free_bits, state, dist, ctl, tiles, mask_stage, log;
     DevBuf targets, starts, offsets, status, cells, activity, order;
     DevBuf jump, segs;   // long walks: jump table (2 * H * W words), segments + counter
+    DevBuf check;        // violation counter of mpn_check
 
     int variant = 0, depth = 32;
     bool auto_tune = true;
@@ -209,7 +210,8 @@ __global__ void k_store_host(const unsigned char *__restrict__ src, unsigned cha
 namespace {
 
 // Mailbox layout (bytes): the control block, then a path total and an error word.
-constexpr size_t kMboxCtl = 0, kMboxTotal = 128, kMboxErr = 136, kMboxWalk = 140, kMboxBytes = 256;
+constexpr size_t kMboxCtl = 0, kMboxTotal = 128, kMboxErr = 136, kMboxWalk = 140, kMboxCheck = 144,
+                 kMboxBytes = 256;
 static_assert(sizeof(Ctl) <= kMboxTotal, "control block must fit the mailbox");
 
 cudaError_t store_host(mpn_ctx *c, void *dst_dev, const void *src, size_t bytes) {
@@ -427,6 +429,7 @@ const char *mpn_status_str(mpn_status s) {
         case MPN_EOVERFLOW: return "distance does not fit the uint16 plane";
         case MPN_EOBSTACLE: return "target on an obstacle";
         case MPN_ESTATE: return "call out of order";
+        case MPN_ECHECK: return "distance plane fails the invariant check";
     }
     return "unknown status";
 }
@@ -439,6 +442,7 @@ const char *mpn_last_error(void) {
 
 mpn_status mpn_create(const uint8_t *mask, int32_t H, int32_t W, int32_t dist_bits, void *stream,
                       mpn_ctx **out) {
+    NvtxRange nvtx_range("mpn_create");
     if (!mask) return MPN_EINVAL;
     mpn_status st = new_ctx(H, W, dist_bits, stream, out);
     if (st != MPN_OK) return st;
@@ -478,6 +482,7 @@ mpn_status mpn_create_packed(const uint32_t *bits, int32_t H, int32_t W, int32_t
 }
 
 mpn_status mpn_set_mask(mpn_ctx *c, const uint8_t *mask) {
+    NvtxRange nvtx_range("mpn_set_mask");
     if (!c) return MPN_EINVAL;
     finish_propagate(c);
     return encode_mask(c, mask);
@@ -591,14 +596,45 @@ static mpn_status run_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, 
     return MPN_OK;
 }
 
+// the invariant check of the context's plane (after its propagation)
+static mpn_status check_plane(mpn_ctx *c, uint64_t *violations) {
+    MPN_TRY(c->check.ensure(sizeof(unsigned long long)));
+    MPN_TRY(launch_check_plane(c->grid(), c->dist_bits, c->last_max_layers,
+                               (unsigned long long *)c->check.p, c->stream));
+    MPN_TRY(to_mbox(c, kMboxCheck, c->check.p, sizeof(uint64_t)));
+    MPN_TRY(cudaStreamSynchronize(c->stream));
+    uint64_t v = 0;
+    memcpy(&v, c->mbox + kMboxCheck, sizeof(v));
+    if (violations) *violations = v;
+    return v ? MPN_ECHECK : MPN_OK;
+}
+
+static bool check_mode() {
+    const char *e = getenv("MPN_CHECK");
+    return e && e[0] == '1';
+}
+
 mpn_status mpn_propagate(mpn_ctx *c, const uint32_t *targets, int32_t n, uint32_t max_layers,
                          uint32_t *layers_run) {
+    NvtxRange nvtx_range("mpn_propagate");
     if (!c || !targets || n < 1) return MPN_EINVAL;
-    return run_propagate(c, targets, n, nullptr, 0u, max_layers, layers_run);
+    mpn_status st = run_propagate(c, targets, n, nullptr, 0u, max_layers, layers_run);
+    if (st == MPN_OK && layers_run && check_mode()) st = check_plane(c, nullptr);
+    return st;
+}
+
+mpn_status mpn_check(mpn_ctx *c, uint64_t *violations) {
+    NvtxRange nvtx_range("mpn_check");
+    if (!c) return MPN_EINVAL;
+    mpn_status st = finish_propagate(c);
+    if (st != MPN_OK) return st;
+    if (!c->propagated) return MPN_ESTATE;
+    return check_plane(c, violations);
 }
 
 mpn_status mpn_propagate_resume(mpn_ctx *c, const void *dist_in, uint32_t from_layer,
                                 uint32_t max_layers, uint32_t *layers_run) {
+    NvtxRange nvtx_range("mpn_propagate_resume");
     if (!c || !dist_in) return MPN_EINVAL;
     if (max_layers && max_layers <= from_layer) return MPN_EINVAL;
     const uint32_t inf = c->dist_bits == 16 ? 0xffffu : 0xffffffffu;
@@ -670,6 +706,7 @@ mpn_status mpn_sync(mpn_ctx *c) {
 }
 
 mpn_status mpn_get_distances(mpn_ctx *c, void *dst, int32_t on_device) {
+    NvtxRange nvtx_range("mpn_get_distances");
     if (!c || !dst) return MPN_EINVAL;
     mpn_status st = finish_propagate(c);
     if (st != MPN_OK) return st;
@@ -766,6 +803,7 @@ mpn_status mpn_trace_lengths(mpn_ctx *c, const uint32_t *starts, int32_t n, uint
 
 static mpn_status trace_any(mpn_ctx *c, const uint32_t *starts, int32_t n, uint64_t *offsets,
                             uint32_t *cells, uint64_t cells_cap, int8_t *status, bool euclid) {
+    NvtxRange nvtx_range("mpn_trace");
     if (!offsets || (n > 0 && !status)) return MPN_EINVAL;
     const uint32_t *ds = nullptr;
     uint64_t total = 0;
@@ -880,6 +918,7 @@ mpn_status mpn_tune_query(int32_t H, int32_t W, int32_t variant, int32_t *depth,
 
 mpn_status mpn_autotune(mpn_ctx *c, const uint32_t *targets, int32_t n, int32_t *variant,
                         int32_t *depth, float *best_ms) {
+    NvtxRange nvtx_range("mpn_autotune");
     if (!c || !targets || n < 1) return MPN_EINVAL;
     static const int kDepths[] = {8, 12, 16, 24, 32};
     int bv = -1, bd = 0;
@@ -952,7 +991,7 @@ void mpn_destroy(mpn_ctx *c) {
     if (c->out_pending && cudaEventSynchronize(c->ev_out) != cudaSuccess) cudaGetLastError();
     DevBuf *bufs[] = {&c->free_bits, &c->state, &c->log, &c->dist, &c->ctl, &c->tiles,
                       &c->mask_stage, &c->targets, &c->starts, &c->offsets, &c->status,
-                      &c->cells, &c->activity, &c->order, &c->jump, &c->segs};
+                      &c->cells, &c->activity, &c->order, &c->jump, &c->segs, &c->check};
     for (DevBuf *b : bufs) b->release();
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);

@@ -759,6 +759,7 @@ mpn_status mpn_batch_set_depth(mpn_batch *b, int32_t depth) {
 mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_t W,
                             const uint32_t *targets, int32_t nt, const uint32_t *starts, int32_t ns,
                             int32_t dist_bits, uint32_t max_layers, uint64_t *ticket) {
+    NvtxRange nvtx_range("mpn_batch_submit");
     if (!b || !mask || !targets || nt < 1 || ns < 0 || (ns > 0 && !starts) || !ticket) return MPN_EINVAL;
     if (H < 1 || W < 1 || (uint64_t)H * W >= 0xffffffffull) return MPN_EINVAL;
     if (dist_bits == MPN_DIST_AUTO) dist_bits = ((int64_t)H * W <= 65535) ? 16 : 32;
@@ -936,6 +937,7 @@ static cudaError_t launch_batch_trace(mpn_batch *b, const HostMaze &m, uint32_t 
 
 // Wait for the stream, then trace every grid that converged in the last round.
 static mpn_status finish_round(mpn_batch *b) {
+    NvtxRange nvtx_range("mpn_batch_finish_round");
     cudaStream_t st = b->stream;
     B_TRY(cudaMemcpyAsync(b->h_bc, b->d_bc, sizeof(BatchCtl), cudaMemcpyDeviceToHost, st));
     B_TRY(cudaMemcpyAsync(b->h_descs, b->d_descs, b->max_slots * sizeof(MazeDesc),
@@ -1078,6 +1080,7 @@ static mpn_status finish_round(mpn_batch *b) {
 }
 
 mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, int32_t *n_done) {
+    NvtxRange nvtx_range("mpn_batch_run");
     if (!b) return MPN_EINVAL;
     cudaStream_t st = b->stream;
     // descriptors and seeds of the grids admitted since the last round
@@ -1202,6 +1205,7 @@ mpn_status mpn_batch_wait(mpn_batch *b, uint64_t ticket, uint32_t max_sweeps, in
 
 mpn_status mpn_batch_result(mpn_batch *b, uint64_t ticket, void *dist, uint64_t *offsets,
                             uint32_t *cells, uint64_t cells_cap, int8_t *status, uint32_t *layers) {
+    NvtxRange nvtx_range("mpn_batch_result");
     if (!b) return MPN_EINVAL;
     auto it = b->mazes.find(ticket);
     if (it == b->mazes.end()) return MPN_EINVAL;

@@ -3,10 +3,20 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "mpn.h"
 
 namespace mpn {
+
+// An NVTX range over a host-side library call (visible to profilers that
+// record NVTX; a no-op otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // error bits the GPU records in Ctl::err
 constexpr uint32_t ERR_TIMEOUT = 1u;    // a grid-wide wait hit its iteration limit
@@ -221,6 +231,10 @@ cudaError_t launch_trace_split(const GridDev &g, int dist_bits, const uint32_t *
                                uint32_t *nseg, cudaStream_t st, uint32_t *err);
 cudaError_t launch_activity(const GridDev &g, int dist_bits, uint32_t L, int32_t *out,
                             cudaStream_t st);
+// Count the cells of the plane that break the distance-map invariants
+// (mpn_check) into *count (device).
+cudaError_t launch_check_plane(const GridDev &g, int dist_bits, uint32_t max_layers,
+                               unsigned long long *count, cudaStream_t st);
 
 // One grid of a batched trace: the paths of many grids are measured, ordered
 // and walked together (a walk takes as long as its path, so the grids' walks

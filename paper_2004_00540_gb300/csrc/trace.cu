@@ -317,6 +317,48 @@ __global__ void __launch_bounds__(TraceWin<DT>::warps * 32)
     }
 }
 
+// ---- on-device invariant check of a distance plane ----
+
+// Cells breaking what a multi-source, 8-connected, unit-cost distance map
+// must satisfy: a reached cell at d > 0 without a free neighbour at d - 1;
+// two reached neighbours more than 1 apart; a reached cell below the layer
+// cap (M, 0 = none) next to an unreached free cell; an obstacle marked
+// reached. Warp-aggregated count.
+template <typename DT>
+__global__ void k_check_plane(GridDev g, uint32_t M, unsigned long long *count) {
+    const DT *dist = reinterpret_cast<const DT *>(g.dist);
+    const DT INF = (DT)~(DT)0;
+    const size_t n = (size_t)g.H * g.W;
+    unsigned bad = 0;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(c / (size_t)g.W), x = (int)(c % (size_t)g.W);
+        const bool free = (g.free_bits[(size_t)y * g.P + (x >> 5)] >> (x & 31)) & 1u;
+        const DT d = dist[c];
+        if (!free) {
+            bad += d != INF;
+            continue;
+        }
+        if (d == INF) continue;   // its reached neighbours check the pair
+        bool down = d == (DT)0, ok = true;
+        for (int q = 0; q < 8; ++q) {
+            const int yy = y + (int)((0xa940u >> (2 * q)) & 3u) - 1;
+            const int xx = x + (int)((0x9224u >> (2 * q)) & 3u) - 1;
+            if (yy < 0 || xx < 0 || yy >= g.H || xx >= g.W) continue;
+            if (!((g.free_bits[(size_t)yy * g.P + (xx >> 5)] >> (xx & 31)) & 1u)) continue;
+            const DT e = dist[(size_t)yy * g.W + xx];
+            if (e == INF) {
+                if (!M || (uint32_t)d < M) ok = false;
+            } else {
+                if ((uint32_t)e + 1u < (uint32_t)d || (uint32_t)d + 1u < (uint32_t)e) ok = false;
+                if ((uint32_t)e + 1u == (uint32_t)d) down = true;
+            }
+        }
+        bad += !(ok && down);
+    }
+    const unsigned tot = __reduce_add_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && tot) atomicAdd(count, (unsigned long long)tot);
+}
+
 // ---- long walks in segments ----
 
 // succ[c] = the next cell of the walk from c (the first neighbour in
@@ -721,6 +763,17 @@ cudaError_t launch_trace(const GridDev &g, int dist_bits, const uint32_t *starts
         k_trace<uint32_t, true><<<(n + w - 1) / w, w * 32, 0, st>>>(g, starts, n, offsets, status, cells,
                                                                     nullptr, nullptr, err, ord);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_plane(const GridDev &g, int dist_bits, uint32_t max_layers,
+                               unsigned long long *count, cudaStream_t st) {
+    const size_t n = (size_t)g.H * g.W;
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    count_launch();
+    if (dist_bits == 16) k_check_plane<uint16_t><<<grid_for(n, 256), 256, 0, st>>>(g, max_layers, count);
+    else k_check_plane<uint32_t><<<grid_for(n, 256), 256, 0, st>>>(g, max_layers, count);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmpn.so")
 
-MPN_OK, MPN_EINVAL, MPN_ENOMEM, MPN_ECUDA, MPN_ETIMEOUT, MPN_EOVERFLOW, MPN_EOBSTACLE, MPN_ESTATE = range(8)
+(MPN_OK, MPN_EINVAL, MPN_ENOMEM, MPN_ECUDA, MPN_ETIMEOUT, MPN_EOVERFLOW, MPN_EOBSTACLE, MPN_ESTATE,
+ MPN_ECHECK) = range(9)
 MPN_DIST_AUTO, MPN_DIST_U16, MPN_DIST_U32 = 0, 16, 32
 MPN_UNREACHED16, MPN_UNREACHED32 = 0xFFFF, 0xFFFFFFFF
 MPN_PATH_OK, MPN_PATH_UNREACHABLE, MPN_PATH_ON_OBSTACLE = 0, 1, 2
@@ -31,7 +32,7 @@ EXPORTS = (
     "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_submit", "mpn_batch_run",
     "mpn_batch_poll", "mpn_batch_wait", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
     "mpn_batch_stats", "mpn_batch_destroy", "mpn_autotune", "mpn_trace_euclid",
-    "mpn_nearest_targets", "mpn_last_error", "mpn_tune_query", "mpn_propagate_resume",
+    "mpn_nearest_targets", "mpn_last_error", "mpn_tune_query", "mpn_propagate_resume", "mpn_check",
 )
 MPN_BATCH_PENDING, MPN_BATCH_DONE, MPN_BATCH_FAILED = 0, 1, 2
 
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
             "mpn_propagate": ([vp, vp, i32, u32, ctypes.POINTER(u32)], ctypes.c_int),
             "mpn_propagate_plain": ([vp, vp, i32, u32, i32, ctypes.POINTER(u32)], ctypes.c_int),
             "mpn_propagate_resume": ([vp, vp, u32, u32, ctypes.POINTER(u32)], ctypes.c_int),
+            "mpn_check": ([vp, ctypes.POINTER(u64)], ctypes.c_int),
             "mpn_get_distances": ([vp, vp, i32], ctypes.c_int),
             "mpn_get_distances_async": ([vp, vp, vp], ctypes.c_int),
             "mpn_get_activity": ([vp, u32, vp, i32], ctypes.c_int),
@@ -144,7 +146,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
 
 def status_name(s: int) -> str:
     names = ["MPN_OK", "MPN_EINVAL", "MPN_ENOMEM", "MPN_ECUDA", "MPN_ETIMEOUT", "MPN_EOVERFLOW",
-             "MPN_EOBSTACLE", "MPN_ESTATE"]
+             "MPN_EOBSTACLE", "MPN_ESTATE", "MPN_ECHECK"]
     return names[s] if 0 <= s < len(names) else f"status {s}"
 
 
@@ -227,6 +229,16 @@ def mpn_propagate_resume(ctx, dist_in, from_layer: int, max_layers: int = 0, wai
         return int(lr.value)
     _check(load().mpn_propagate_resume(ctx, p, from_layer, max_layers, None), "mpn_propagate_resume")
     return None
+
+
+def mpn_check(ctx) -> int:
+    """Cells of the last propagation's plane that break the distance-map
+    invariants (0 for a correct plane)."""
+    v = ctypes.c_uint64(0)
+    st = load().mpn_check(ctx, ctypes.byref(v))
+    if st not in (MPN_OK, MPN_ECHECK):
+        raise MPNError(st, "mpn_check")
+    return int(v.value)
 
 
 def mpn_propagate_plain(ctx, targets, max_layers: int = 0, check_every: int = 1):

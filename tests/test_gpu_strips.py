@@ -63,3 +63,33 @@ def test_strips_on_one_gpu_equal_oracle(world, k):
     got, L = strips.LocalComms.solve(m2, t2, world, k, engines, max_layers=61)
     want, Lw = oracle.bfs(m2, t2, max_layers=61)
     assert L == Lw and np.array_equal(got, want)
+
+
+def test_invariant_check_accepts_solves_and_flags_a_bad_plane(monkeypatch):
+    """mpn_check (the on-device invariant check) finds nothing wrong in solved
+    planes (a maze, a Bernoulli grid, a fixed depth, the MPN_CHECK=1 mode of
+    mpn_propagate), and counts the cells of a plane that is not a distance map:
+    one resumed from a prefix in which two neighbouring cells are 4 apart."""
+    torch = pytest.importorskip("torch")
+    maze = synth.dfs_maze(301, 257, 51)
+    m2 = synth.bernoulli(200, 333, 0.3, 52)
+    for m, n in ((maze, 2), (m2, 4)):
+        t = synth.sample_free(m, n, 53)
+        with pkg.Planner(m, pkg.MPN_DIST_U32) as pl:
+            pl.propagate(t)
+            assert pkg.mpn_check(pl.ctx) == 0
+            pl.propagate(t, max_layers=7)
+            assert pkg.mpn_check(pl.ctx) == 0
+        monkeypatch.setenv("MPN_CHECK", "1")
+        with pkg.Planner(m, pkg.MPN_DIST_U32) as pl:
+            assert pl.propagate(t) == oracle.bfs(m, t)[1]
+        monkeypatch.delenv("MPN_CHECK")
+    e = synth.empty(40, 50)
+    plane = np.full((40, 50), 0xFFFFFFFF, np.uint32)
+    plane[0, 0] = 0
+    plane[0, 2] = 5                  # no cell at 4 next to it: not a distance map
+    with pkg.Planner(e, pkg.MPN_DIST_U32) as pl:
+        pkg.mpn_propagate_resume(pl.ctx, plane, 5)
+        assert pkg.mpn_check(pl.ctx) > 0
+        st = pkg.load().mpn_check(pl.ctx, None)
+        assert st == pkg.MPN_ECHECK

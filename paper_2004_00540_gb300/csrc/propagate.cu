@@ -484,10 +484,12 @@ __device__ __forceinline__ uint32_t spread_nibble(uint32_t n) {   // bit i -> bi
     return (n * 0x204081u) & 0x01010101u;
 }
 
-// shared memory words of a band of `rows` rows: layers (33 per word), then
-// reached and covered bits per word
+// shared memory words of a band of `rows` rows: 16-bit layer codes (34 per
+// word: the pad spreads a warp's words over the banks), then reached and
+// covered bits per word. A tile in 32-bit mode uses half as many rows per band
+// (33 words per word of cells) in the same room.
 __host__ __device__ inline size_t decode_band_words(int rows, int txw) {
-    return (size_t)rows * txw * 35;
+    return (size_t)rows * txw * 17 + 2 * (size_t)rows * txw;
 }
 
 template <typename DT, int TXW>
@@ -495,14 +497,17 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
     extern __shared__ __align__(16) uint32_t buf[];
     __shared__ uint32_t s_gh[kDecodeBatch], s_cnt[kDecodeBatch], s_lay[kDecodeBatch];
     __shared__ uint32_t s_start[kDecodeBatch + 1];
-    __shared__ uint32_t s_nvis, s_chain, s_bad;
+    __shared__ uint32_t s_nvis, s_chain, s_bad, s_lo, s_narrow;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const GridDev &g = p.g;
     const int TY = p.TY;
-    constexpr int CW = TXW * 32, RW = TXW * 33;   // RW: buffer words per row
+    constexpr int CW = TXW * 32, RW = TXW * 33;   // RW: buffer words per row (32-bit mode)
+    constexpr int RH = TXW * 34;                  // halves per row (16-bit mode)
     const uint32_t cap = p.log_chunks * kLogChunk;
     constexpr uint32_t kNone = 0xffffffffu;
-    uint32_t *sV = buf + (size_t)band_rows * RW;          // reached bits per word
+    constexpr uint16_t kNone16 = 0xffffu, kKeep16 = 0xfffeu;
+    uint16_t *b16 = reinterpret_cast<uint16_t *>(buf);
+    uint32_t *sV = buf + (size_t)band_rows * TXW * 17;    // reached bits per word
     uint32_t *sC = sV + (size_t)band_rows * TXW;          // bits covered by entries per word
     const int ntiles = p.ntx * p.nty;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -513,10 +518,29 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
         // slot threadIdx.x (read only below nv)
         const uint4 slot = threadIdx.x < slots ? p.tile_vis[(size_t)t * kTileSlots + threadIdx.x]
                                                     : make_uint4(0u, 0u, 0u, 0u);
-        for (int b0 = 0; b0 < rows; b0 += band_rows) {
-            const int br = min(band_rows, rows - b0);
+        __syncthreads();   // the previous tile's s_lo / s_narrow are no longer read
+        if (threadIdx.x == 0) {
+            // 16-bit codes (layer - the tile's first logged layer) when the
+            // tile's layers span less than 16 bits: its first logged visit is
+            // in slot 0, its last is the head of the header chain
+            uint32_t lo = 0u, narrow = 1u;
+            if (nv) {
+                lo = slot.z;
+                const uint32_t h = p.tile_head[t];
+                const uint32_t hi = (h && h - 1u < cap) ? p.log[(size_t)(h - 1u) * kLogFields + 2] : lo;
+                narrow = hi >= lo && (hi - lo) + 31u <= 0xfffdu;
+            }
+            s_lo = lo;
+            s_narrow = narrow;
+        }
+        __syncthreads();
+        const bool narrow = s_narrow != 0u;
+        const uint32_t lo = s_lo;
+        const int bstep = narrow ? band_rows : max(1, band_rows / 2);
+        for (int b0 = 0; b0 < rows; b0 += bstep) {
+            const int br = min(bstep, rows - b0);
             {
-                const int n = br * RW;
+                const int n = narrow ? br * TXW * 17 : br * RW;
                 uint4 *b4 = reinterpret_cast<uint4 *>(buf);
                 for (int i = threadIdx.x; i < n / 4; i += 256) b4[i] = make_uint4(kNone, kNone, kNone, kNone);
                 for (int i = (n & ~3) + threadIdx.x; i < n; i += 256) buf[i] = kNone;
@@ -603,26 +627,49 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
                     for (int q = 3; q >= 0; --q) B[q] ^= B[q + 1];   // Gray -> binary, bit-sliced
                     const uint32_t w = (row - (uint32_t)b0) * (uint32_t)TXW + word;
                     atomicOr(&sC[w], nb);
-                    uint32_t *dst = buf + (row - (uint32_t)b0) * (uint32_t)RW + word * 33u;
+                    if (narrow) {
+                        uint16_t *dst = b16 + (row - (uint32_t)b0) * (uint32_t)RH + word * 34u;
+                        const uint32_t l16 = lay - lo;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        uint32_t off4 = 0u;
+                        for (int q = 0; q < 8; ++q) {
+                            uint32_t off4 = 0u;
 #pragma unroll
-                        for (int bb = 0; bb < 5; ++bb) off4 += spread_nibble((B[bb] >> (4 * q)) & 0xfu) << bb;
+                            for (int bb = 0; bb < 5; ++bb) off4 += spread_nibble((B[bb] >> (4 * q)) & 0xfu) << bb;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            if ((nb >> (4 * q + i)) & 1u) dst[4 * q + i] = lay + ((off4 >> (8 * i)) & 0xffu);
+                            for (int i = 0; i < 4; ++i)
+                                if ((nb >> (4 * q + i)) & 1u) dst[4 * q + i] = (uint16_t)(l16 + ((off4 >> (8 * i)) & 0xffu));
+                        }
+                    } else {
+                        uint32_t *dst = buf + (row - (uint32_t)b0) * (uint32_t)RW + word * 33u;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            uint32_t off4 = 0u;
+#pragma unroll
+                            for (int bb = 0; bb < 5; ++bb) off4 += spread_nibble((B[bb] >> (4 * q)) & 0xfu) << bb;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if ((nb >> (4 * q + i)) & 1u) dst[4 * q + i] = lay + ((off4 >> (8 * i)) & 0xffu);
+                        }
                     }
                 }
                 done += nb_vis;
                 if (s_bad || nb_vis == 0) break;   // block-uniform
             }
             __syncthreads();
-            // ---- reached cells without an entry keep their value ----
+            // ---- reached cells without an entry keep their value (16-bit
+            // mode: they are not written at all) ----
             for (int i = threadIdx.x; i < br * TXW; i += 256) {
                 uint32_t m = sV[i] & ~sC[i];
                 if (!m) continue;
                 const int r = i / TXW, word = i - r * TXW;
+                if (narrow) {
+                    while (m) {
+                        const int c = __ffs(m) - 1;
+                        m &= m - 1u;
+                        b16[r * RH + word * 34 + c] = kKeep16;
+                    }
+                    continue;
+                }
                 const DT *src = reinterpret_cast<const DT *>(g.dist) + (size_t)(ybase + b0 + r) * g.W +
                                 xbase + word * 32;
                 while (m) {
@@ -636,10 +683,18 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
             for (int r = warp; r < br; r += 8) {
                 DT *d = reinterpret_cast<DT *>(g.dist) + (size_t)(ybase + b0 + r) * g.W + xbase + lane;
                 const uint32_t *src = buf + r * RW + lane;
+                const uint16_t *src16 = b16 + r * RH + lane;
 #pragma unroll
                 for (int w = 0; w < TXW; ++w) {   // word w: cells 32 w + lane
                     if (32 * w + lane < cols) {
-                        const uint32_t val = src[33 * w];
+                        uint32_t val;
+                        if (narrow) {
+                            const uint16_t c16 = src16[34 * w];
+                            if (c16 == kKeep16) continue;   // reached without an entry: as it is
+                            val = c16 == kNone16 ? kNone : lo + c16;
+                        } else {
+                            val = src[33 * w];
+                        }
                         if (sizeof(DT) == 2) {
                             if (val != kNone && val > 0xfffeu) atomicOr(&p.ctl->err, ERR_OVERFLOW);
                             d[32 * w] = (DT)(val > 0xfffeu ? 0xffffu : val);
@@ -1122,10 +1177,10 @@ cudaError_t launch_propagate(int v, int dist_bits, const PropParams &p, int bloc
 template <int TXW>
 static cudaError_t launch_decode_txw(const PropParams &p, int dist_bits, int sm_count, uint32_t slots,
                                      cudaStream_t st) {
-    // a band of at most 32 KB of layers (half an interior for the usual tile
-    // shapes: six blocks per SM keep more loads in flight than three blocks
-    // with whole interiors), plus its reached and covered words
-    int band = (32 * 1024) / (TXW * 33 * 4);
+    // a band of at most 36 KB with 16-bit layer codes (a whole 80-row
+    // interior for the usual tile shapes, so each log entry is read once, and
+    // six blocks per SM), plus its reached and covered words
+    int band = (36 * 1024) / (TXW * (34 * 2 + 8));
     band = band < 1 ? 1 : (band > p.TY ? p.TY : band);
     const size_t smem = decode_band_words(band, TXW) * sizeof(uint32_t);
     static std::once_flag once;

@@ -493,11 +493,11 @@ __host__ __device__ inline size_t decode_band_words(int rows, int txw) {
 }
 
 template <typename DT, int TXW>
-__global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows, uint32_t slots) {
+__global__ void __launch_bounds__(256, 6) k_log_decode(PropParams p, int band_rows, uint32_t slots) {
     extern __shared__ __align__(16) uint32_t buf[];
     __shared__ uint32_t s_gh[kDecodeBatch], s_cnt[kDecodeBatch], s_lay[kDecodeBatch];
     __shared__ uint32_t s_start[kDecodeBatch + 1];
-    __shared__ uint32_t s_nvis, s_chain, s_bad, s_lo, s_narrow;
+    __shared__ uint32_t s_nvis, s_chain, s_bad, s_lo, s_narrow, s_max;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const GridDev &g = p.g;
     const int TY = p.TY;
@@ -507,6 +507,8 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
     constexpr uint32_t kNone = 0xffffffffu;
     constexpr uint16_t kNone16 = 0xffffu, kKeep16 = 0xfffeu;
     uint16_t *b16 = reinterpret_cast<uint16_t *>(buf);
+    uint32_t thr_max = 0u;   // the largest layer of this thread's log entries (the layer count L)
+    if (threadIdx.x == 0) s_max = 0u;
     uint32_t *sV = buf + (size_t)band_rows * TXW * 17;    // reached bits per word
     uint32_t *sC = sV + (size_t)band_rows * TXW;          // bits covered by entries per word
     const int ntiles = p.ntx * p.nty;
@@ -625,6 +627,18 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
                     uint32_t B[5] = {a.z, a.w, b.x, b.y, b.z};
 #pragma unroll
                     for (int q = 3; q >= 0; --q) B[q] ^= B[q + 1];   // Gray -> binary, bit-sliced
+                    {   // the entry's last layer: a bit-sliced maximum over its reached cells
+                        uint32_t cand = nb, m = 0u;
+#pragma unroll
+                        for (int q = 4; q >= 0; --q) {
+                            const uint32_t hit = cand & B[q];
+                            if (hit) {
+                                m |= 1u << q;
+                                cand = hit;
+                            }
+                        }
+                        if (nb) thr_max = max(thr_max, lay + m);
+                    }
                     const uint32_t w = (row - (uint32_t)b0) * (uint32_t)TXW + word;
                     atomicOr(&sC[w], nb);
                     if (narrow) {
@@ -695,6 +709,7 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
                         } else {
                             val = src[33 * w];
                         }
+
                         if (sizeof(DT) == 2) {
                             if (val != kNone && val > 0xfffeu) atomicOr(&p.ctl->err, ERR_OVERFLOW);
                             d[32 * w] = (DT)(val > 0xfffeu ? 0xffffu : val);
@@ -707,6 +722,12 @@ __global__ void __launch_bounds__(256) k_log_decode(PropParams p, int band_rows,
             __syncthreads();   // before the next band or tile refills the buffer
         }
     }
+    // the layer count: the largest layer of any entry (visits that wrote their
+    // distances themselves counted theirs in the propagation kernel)
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, thr_max);
+    if (lane == 0 && wm) atomicMax(&s_max, wm);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_max) atomicMax(&p.ctl->max_layer, s_max);
 }
 
 // ---- warp-specialised variant: a producer warp stages regions with TMA ----

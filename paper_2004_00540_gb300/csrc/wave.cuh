@@ -366,10 +366,13 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WP
 
     // ---- the last layer at which one of this thread's cells was reached ----
     // (a bit-sliced maximum of t over the reached cells, from the planes
-    // turned from Gray code into binary, most significant bit first)
+    // turned from Gray code into binary, most significant bit first). Only
+    // when the visit writes its distances itself: with the activation log the
+    // decode sees every cell's layer and takes the maximum there.
+    const int chunk = lg.log ? *lg.s_chunk : -1;   // block-uniform
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-        if (!NB[s]) continue;
+        if (chunk >= 0 || !NB[s]) continue;
         uint32_t B[5];
         B[4] = P[4][s];
 #pragma unroll
@@ -402,7 +405,6 @@ __device__ __forceinline__ void visit_core(const Visit &v, VisitSmem<RXW, NW, WP
     *lastj_out = lastj;
 
     // ---- distances of the cells first reached in this visit ----
-    const int chunk = lg.log ? *lg.s_chunk : -1;   // block-uniform
     if (chunk >= 0) {
         // one activation-log entry per changed word: the warp reserves its
         // entries with one shared-memory atomic and writes each as two 16-byte

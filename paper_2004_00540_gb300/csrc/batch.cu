@@ -63,6 +63,7 @@ struct BatchParams {
     uint32_t round_sweeps;  // 0 = until every grid converged
     uint32_t spin_limit;
     uint32_t lookahead;     // 1: blocks waiting at a sweep's end run ready tiles of the next
+    uint32_t *rank;         // kRankWords counters, zero at the launch (block ranks)
 };
 
 struct SeedJob {
@@ -176,14 +177,18 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
     const uint32_t G = gridDim.x;
     const size_t MT = p.max_tiles;
     sm.zero_pad();   // (the first barrier below publishes it)
+    int rk = 0;   // thread 0: this block's rank in the lists' fixed deal (wave::block_rank)
     if (threadIdx.x == 0) {
+        rk = wave::block_rank(p.rank, p.spin_limit, &ctl->err);
+        s_dec[0] = rk >= 0 ? 0 : -3;
         // the round's first sweep; later sweeps read their list length and
         // first entry after the grid barrier, with the end-of-round test
         s_len = ld_acquire(&ctl->list_len[s0 % kListSlots]);
-        s_tile = (blockIdx.x < s_len) ? take_entry_b(p.lists + (size_t)(s0 % kListSlots) * MT, blockIdx.x) : -1;
+        s_tile = (rk >= 0 && (uint32_t)rk < s_len) ? take_entry_b(p.lists + (size_t)(s0 % kListSlots) * MT, (uint32_t)rk) : -1;
         s_done_t = -1;
     }
     __syncthreads();
+    if (s_dec[0] == -3) return;   // a wait ran out (recorded)
 
     // one thread: publish the done stamp of the last visited tile (release:
     // the visit's writes, block barriers before, come with it)
@@ -250,7 +255,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
         const bool la_s = p.lookahead && len > G / 4;
         int t = s_tile;
         if (t < 0 && threadIdx.x == 0) {
-            const uint32_t i = pend_mine >= 0 ? (uint32_t)pend_mine : G + atomicAdd(work, 1u);
+            // (a list no longer than the grid has no entries past the blocks' own)
+            const uint32_t i = pend_mine >= 0 ? (uint32_t)pend_mine : (len > G ? G + atomicAdd(work, 1u) : len);
             pend_mine = -1;
             s_tile = (i < len) ? take_entry_b(list, i) : -1;
         }
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
                     next_i = (uint32_t)pend_mine;
                     pend_mine = -1;
                 } else {
-                    next_i = G + atomicAdd(work, 1u);
+                    next_i = len > G ? G + atomicAdd(work, 1u) : len;
                 }
                 s_mask[vq] = 0u;
                 s_lastj[vq] = 0u;
@@ -336,7 +342,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
                 if (lane == 0) {
                     int fe = -1, me = -1;
                     if (look) {
-                        if (!fixed_taken) fe = (int)ld_relaxed(list1 + blockIdx.x) - 1;
+                        if (!fixed_taken) fe = (int)ld_relaxed(list1 + rk) - 1;
                         if (pend_mine >= 0 && (uint32_t)pend_mine < MT) me = (int)ld_relaxed(list1 + pend_mine) - 1;
                     }
                     if (ld_acquire(&ctl->bar_count) >= target) {
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
                     } else if (look) {
                         if (fe >= 0 && (me < 0 || !toggle)) {
                             cand = fe;
-                            cidx = (int)blockIdx.x;
+                            cidx = rk;
                         } else if (me >= 0) {
                             cand = me;
                             cidx = pend_mine;
@@ -375,7 +381,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
                         dec = cand;
                         if (lane == 0) {
                             wave::st_relaxed(list1 + cidx, 0u);
-                            if (cidx == (int)blockIdx.x && !fixed_taken) fixed_taken = true;
+                            if (cidx == rk && !fixed_taken) fixed_taken = true;
                             else pend_mine = -1;
                         }
                     }
@@ -433,7 +439,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             // one read gives the end-of-round test and the next sweep's list
             // length; the block's own entry of it comes alongside
             const uint32_t nlen = ld_relaxed(&ctl->list_len[sl1]);
-            const uint32_t fe = fixed_taken ? 0u : ld_relaxed(list1 + blockIdx.x);
+            const uint32_t fe = fixed_taken ? 0u : ld_relaxed(list1 + rk);
             const unsigned done = (nlen == 0u) || last;
             if (done && blockIdx.x == 0) {
                 p.bc->next_sweep = s + 1;
@@ -450,9 +456,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
             s_len = nlen;
             int first = -1;
             if (!done) {   // (a finished round leaves list s + 1 to the next round)
-                if (!fixed_taken && blockIdx.x < nlen && fe) {
+                if (!fixed_taken && (uint32_t)rk < nlen && fe) {
                     first = (int)fe - 1;
-                    wave::st_relaxed(list1 + blockIdx.x, 0u);
+                    wave::st_relaxed(list1 + rk, 0u);
                 }
                 if (first < 0 && pend_mine >= 0) {
                     if ((uint32_t)pend_mine < nlen) first = take_entry_b(list1, (uint32_t)pend_mine);
@@ -607,6 +613,7 @@ struct mpn_batch {
     MazeDesc *d_descs = nullptr;
     uint32_t *d_tile_maze = nullptr, *d_stamps = nullptr, *d_done = nullptr, *d_lists = nullptr;
     BatchCtl *d_bc = nullptr;
+    uint32_t *d_rank = nullptr;       // block-rank counters, zeroed before every round
     SeedJob *d_jobs = nullptr;
     MazeDesc *h_descs = nullptr;      // pinned mirror for readback
     BatchCtl *h_bc = nullptr;         // pinned
@@ -720,6 +727,7 @@ mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_done, (size_t)b->max_tiles * 4);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_lists, (size_t)b->max_tiles * kListSlots * 4);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bc, sizeof(BatchCtl));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_rank, kRankWords * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_jobs, b->max_slots * sizeof(SeedJob));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_descs, b->max_slots * sizeof(MazeDesc));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_bc, sizeof(BatchCtl));
@@ -857,6 +865,8 @@ static cudaError_t enqueue_round(mpn_batch *b, const BatchParams &p) {
     cudaStream_t st = b->stream;
     k_round_prep<<<1, 1, 0, st>>>(b->d_bc);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b->d_rank, 0, kRankWords * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     // external records, so that they time the round also when it is captured
     e = cudaEventRecordWithFlags(b->ev0, st, cudaEventRecordExternal);
@@ -1140,6 +1150,7 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, 
     p.lists = b->d_lists;
     p.max_tiles = b->max_tiles;
     p.bc = b->d_bc;
+    p.rank = b->d_rank;
     p.round_sweeps = max_sweeps;
     p.spin_limit = 1u << 24;
     p.lookahead = 1;
@@ -1307,6 +1318,7 @@ void mpn_batch_destroy(mpn_batch *b) {
     cudaFree(b->d_done);
     cudaFree(b->d_lists);
     cudaFree(b->d_bc);
+    cudaFree(b->d_rank);
     cudaFree(b->d_jobs);
     if (b->h_descs) cudaFreeHost(b->h_descs);
     if (b->h_bc) cudaFreeHost(b->h_bc);

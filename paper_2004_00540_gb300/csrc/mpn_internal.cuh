@@ -80,6 +80,10 @@ constexpr int kListSlots = 4;
 // latest log header, logged-visit count, lists
 constexpr int kTileQueueWords = kStampSlots + 1 + 2 + kListSlots;
 
+// Counters behind the block ranks of a persistent launch (wave::block_rank):
+// 256 per-SM counters, 32 per-place counters and a barrier counter.
+constexpr uint32_t kRankWords = 320;
+
 struct PropParams {
     GridDev g;
     uint32_t *stamps;            // kStampSlots arrays of ntiles: 1 + sweep the tile is queued for
@@ -100,6 +104,7 @@ struct PropParams {
     uint32_t sweep_cap;          // more sweeps than this is an error
     uint32_t *log;               // activation log (log_chunks chunks), or null
     uint32_t log_chunks;
+    uint32_t *rank;              // kRankWords counters, zero at the launch (block ranks), or null
 };
 
 // Activation log: instead of writing distances during a tile visit, the visit
@@ -124,28 +129,31 @@ constexpr uint32_t kLogChunk = 4096;
 constexpr uint32_t kTileSlots = 64;
 constexpr uint32_t kLogFields = 8;
 
-// Words of the tile-queue buffer for ntiles tiles: kTileQueueWords per tile
+// Words of the tile-queue buffer for ntiles tiles: the block-rank counters
+// (kRankWords), kTileQueueWords per tile
 // (stamps, done, latest header, logged-visit count, lists), then, 16-byte
 // aligned, kTileSlots visit slots of 4 words per tile when with_slots.
 inline size_t tile_queue_words(size_t ntiles, bool with_slots) {
-    const size_t head = (kTileQueueWords * ntiles + 3) & ~(size_t)3;
+    const size_t head = (kRankWords + kTileQueueWords * ntiles + 3) & ~(size_t)3;
     return head + (with_slots ? 4 * (size_t)kTileSlots * ntiles : 0);
 }
 
 // Point p's queue arrays into buf (tile_queue_words(ntiles, with_slots)
-// words, 16-byte aligned). The first kTileQueueWords * ntiles words must be
-// zero before each propagation (returned in *clear_words).
+// words, 16-byte aligned): the block-rank counters, then the per-tile arrays.
+// The first kRankWords + kTileQueueWords * ntiles words must be zero before
+// each propagation (returned in *clear_words).
 inline void layout_tile_queue(uint32_t *buf, size_t ntiles, bool with_slots, PropParams *p,
                               size_t *clear_words) {
-    p->stamps = buf;
-    p->done = buf + kStampSlots * ntiles;
+    p->rank = buf;
+    p->stamps = buf + kRankWords;
+    p->done = p->stamps + kStampSlots * ntiles;
     p->tile_head = p->done + ntiles;
     p->tile_nv = p->tile_head + ntiles;
     p->lists = p->tile_nv + ntiles;
     p->tile_vis = with_slots
-                      ? reinterpret_cast<uint4 *>(buf + ((kTileQueueWords * ntiles + 3) & ~(size_t)3))
+                      ? reinterpret_cast<uint4 *>(buf + ((kRankWords + kTileQueueWords * ntiles + 3) & ~(size_t)3))
                       : nullptr;
-    *clear_words = kTileQueueWords * ntiles;
+    *clear_words = kRankWords + kTileQueueWords * ntiles;
 }
 
 struct VariantDesc {

@@ -38,7 +38,7 @@ constexpr int kNaDepth = 32;
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kNaPlaneBytes = align256(kNaPlaneWords * sizeof(uint32_t));
-constexpr size_t kNaTileBytes = align256((kTileQueueWords * kNaMaxTiles + 3) / 4 * 4 * sizeof(uint32_t));
+constexpr size_t kNaTileBytes = align256((kRankWords + kTileQueueWords * kNaMaxTiles + 3) / 4 * 4 * sizeof(uint32_t));
 constexpr size_t kNaCtlBytes = align256(sizeof(Ctl));
 constexpr size_t kNaScratchBytes = 5 * kNaPlaneBytes + kNaTileBytes + kNaCtlBytes;
 

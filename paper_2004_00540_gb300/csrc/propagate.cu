@@ -133,16 +133,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
     v.TXW = p.TXW;
     v.k = p.k;
     const size_t ntl = (size_t)ntiles;
-    const uint32_t G = gridDim.x;   // <= ntiles, so list + blockIdx.x is inside every list
+    const uint32_t G = gridDim.x;   // <= ntiles, so list + rk is inside every list
+    int rk = 0;   // thread 0: this block's rank in the lists' fixed deal (wave::block_rank)
     if (threadIdx.x == 0) {
-        // sweep 0: entry blockIdx.x of the seeded list is this block's first tile
+        rk = wave::block_rank(p.rank, p.spin_limit, &ctl->err);
+        s_ok = rk >= 0;
+        // sweep 0: entry rk of the seeded list is this block's first tile
         s_len = ld_acquire(&ctl->list_len[0]);
-        s_tile = (blockIdx.x < s_len) ? take_entry(p.lists, blockIdx.x) : -1;
+        s_tile = (rk >= 0 && (uint32_t)rk < s_len) ? take_entry(p.lists, (uint32_t)rk) : -1;
         s_chunk = -1;
         s_cursor = 0u;
         s_done_t = -1;
     }
     __syncthreads();
+    if (!s_ok) return;   // a wait ran out (recorded)
 
     // thread 0, before a visit of tile t: room in the log chunk, the header
     // slot, the tile's chain so far (its previous visit has finished)
@@ -228,7 +232,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
         // barrier comes first)
         int t = s_tile;
         if (t < 0 && threadIdx.x == 0) {
-            const uint32_t i = pend_mine >= 0 ? (uint32_t)pend_mine : G + atomicAdd(work, 1u);
+            // (a list no longer than the grid has no entries past the blocks' own)
+            const uint32_t i = pend_mine >= 0 ? (uint32_t)pend_mine : (len > G ? G + atomicAdd(work, 1u) : len);
             pend_mine = -1;
             s_tile = (i < len) ? take_entry(list, i) : -1;
         }
@@ -248,7 +253,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                     next_i = (uint32_t)pend_mine;
                     pend_mine = -1;
                 } else {
-                    next_i = G + atomicAdd(work, 1u);
+                    next_i = len > G ? G + atomicAdd(work, 1u) : len;
                 }
                 s_mask[vq] = 0u;   // last read two visits ago, before the previous visit's first barrier
                 log_begin(t);
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                     // (a candidate read before it is checked again below)
                     int fe = -1, me = -1;
                     if (look) {
-                        if (!fixed_taken) fe = (int)ld_relaxed(list1 + blockIdx.x) - 1;
+                        if (!fixed_taken) fe = (int)ld_relaxed(list1 + rk) - 1;
                         if (pend_mine >= 0 && (uint32_t)pend_mine < ntl)
                             me = (int)ld_relaxed(list1 + pend_mine) - 1;
                     }
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                         // candidates: this block's own first entry, and one claimed entry
                         if (fe >= 0 && (me < 0 || !toggle)) {
                             cand = fe;
-                            cidx = (int)blockIdx.x;
+                            cidx = rk;
                         } else if (me >= 0) {
                             cand = me;
                             cidx = pend_mine;
@@ -353,7 +358,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
                         dec = cand;
                         if (lane == 0) {
                             wave::st_relaxed(list1 + cidx, 0u);
-                            if (cidx == (int)blockIdx.x && !fixed_taken) fixed_taken = true;
+                            if (cidx == rk && !fixed_taken) fixed_taken = true;
                             else pend_mine = -1;
                         }
                     }
@@ -419,7 +424,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             // next sweep's list length
             // (the barrier's completion was read with acquire; these two loads go out together)
             const uint32_t nlen = ld_relaxed(&ctl->list_len[slot1]);
-            const uint32_t fe = fixed_taken ? 0u : ld_relaxed(list1 + blockIdx.x);
+            const uint32_t fe = fixed_taken ? 0u : ld_relaxed(list1 + rk);
             unsigned done = (nlen == 0u) || (p.max_layers && l1 >= p.max_layers);
             if (!done && s + 1 >= p.sweep_cap) {
                 atomicOr(&ctl->err, ERR_SWEEPS);
@@ -436,9 +441,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_propagate(PropParams p) {
             // this block's first tile of sweep s + 1: its own entry (unless it
             // ran already), else the entry it claimed while waiting
             int first = -1;
-            if (!fixed_taken && blockIdx.x < nlen && fe) {
+            if (!fixed_taken && (uint32_t)rk < nlen && fe) {
                 first = (int)fe - 1;
-                wave::st_relaxed(list1 + blockIdx.x, 0u);
+                wave::st_relaxed(list1 + rk, 0u);
             }
             if (first < 0 && pend_mine >= 0) {
                 if ((uint32_t)pend_mine < nlen) first = take_entry(list1, (uint32_t)pend_mine);
@@ -880,6 +885,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, 2)
                     return true;
                 };
                 auto claim = [&]() -> int {
+                    if (len <= G) return -1;   // no entries past the blocks' own
                     const uint32_t i = G + atomicAdd(work, 1u);
                     return (i < len) ? take_entry(list, i) : -1;
                 };

@@ -87,6 +87,39 @@ __device__ __forceinline__ bool grid_barrier(Ctl *c, unsigned target, unsigned s
     return *s_ok != 0;
 }
 
+// Rank of this block for the fixed one-entry-per-block deal of a tile list
+// (entry r goes to the block of rank r without an atomic). The hardware puts
+// consecutive block indices on the same SM (on a GB300, blocks 0..11 of a
+// three-per-SM grid share four SMs), so a short list dealt by block index
+// would run several visits on one SM while most SMs idle. Ranked by the
+// block's place among the blocks of its SM first, the first block of every
+// SM comes before any second one. Thread 0 of every block of the grid calls
+// it once, at the start; cnt holds kRankWords counters that are zero at the
+// launch (256 per SM, 32 per place, one barrier). The ranks are a permutation
+// of 0 .. gridDim.x - 1. A wait past spin_limit records ERR_TIMEOUT in *err
+// and returns -1; without counters (cnt null) the rank is the block index.
+__device__ __forceinline__ int block_rank(uint32_t *cnt, unsigned spin_limit, uint32_t *err) {
+    if (!cnt) return (int)blockIdx.x;
+    unsigned nsm, sid;
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sid));
+    if (nsm > 256u) return (int)blockIdx.x;   // (the same for every block)
+    const unsigned place = atomicAdd(cnt + sid, 1u);   // < 32 resident blocks per SM
+    const unsigned pos = atomicAdd(cnt + 256 + place, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(cnt + 288) : "memory");
+    unsigned spins = 0;
+    while (ld_acquire(cnt + 288) < gridDim.x) {
+        if (++spins > spin_limit || ((spins & 63u) == 0u && (ld_acquire(err) & ERR_TIMEOUT))) {
+            atomicOr(err, ERR_TIMEOUT);
+            return -1;
+        }
+        if (spins > 8) __nanosleep(32);
+    }
+    unsigned base = 0;
+    for (unsigned j = 0; j < place; ++j) base += ld_relaxed(cnt + 256 + j);
+    return (int)(base + pos);
+}
+
 // 3x3 dilation along the row: v | v shifted one cell left | one cell right,
 // with the carries from the neighbouring words of the same row (the lanes of
 // one row group hold consecutive words). At the region's outer words the

@@ -277,7 +277,7 @@ mpn_status mpn_set_tuning(mpn_ctx *ctx, int32_t variant, int32_t depth);
 /*
  * Autotuner (no counterpart in the paper; its run time depends on L and n,
  * Results, "Run-time"): time every compiled tile shape and every depth in {8, 12, 16,
- * 24, 32} (where the shape allows it) by propagating from these targets on
+ * 20, 24, 28, 32} (where the shape allows it) by propagating from these targets on
  * this context's grid; keep the fastest for the context and record, for the
  * grid's size bucket ceil(log2(max(H, W))), the fastest depth per shape and
  * the fastest shape overall. Contexts created later with automatic tiling,

@@ -920,7 +920,7 @@ mpn_status mpn_autotune(mpn_ctx *c, const uint32_t *targets, int32_t n, int32_t 
                         int32_t *depth, float *best_ms) {
     NvtxRange nvtx_range("mpn_autotune");
     if (!c || !targets || n < 1) return MPN_EINVAL;
-    static const int kDepths[] = {8, 12, 16, 24, 32};
+    static const int kDepths[] = {8, 12, 16, 20, 24, 28, 32};
     int bv = -1, bd = 0;
     float bms = 0.f;
     for (int v = 0; v < num_variants(); ++v) {

@@ -1113,6 +1113,7 @@ constexpr VariantDesc kVariants[] = {
     {8, 1, 32, 1, 0},   // 128 rows x 256 cells, 1 row per lane, 1024 threads
     {8, 2, 8, 3, 0, 2},   // 128 rows x 256 cells, 2 words x 2 rows per lane
     {8, 4, 8, 2, 0, 2},   // 256 rows x 256 cells, 2 words x 4 rows per lane
+    {8, 8, 4, 4, 0},    // 128 rows x 256 cells, 4 warps of 8 rows per lane (fewer warps per barrier)
 };
 
 void *variant_fn(int v, int dist_bits) {
@@ -1129,6 +1130,7 @@ void *variant_fn(int v, int dist_bits) {
         case 8: return variant_ptr<8, 1, 32, 1>(u16);
         case 9: return variant_ptr<8, 2, 8, 3, 2>(u16);
         case 10: return variant_ptr<8, 4, 8, 2, 2>(u16);
+        case 11: return variant_ptr<8, 8, 4, 4>(u16);
         default: return nullptr;
     }
 }

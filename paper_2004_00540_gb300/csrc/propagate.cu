@@ -1114,6 +1114,8 @@ constexpr VariantDesc kVariants[] = {
     {8, 2, 8, 3, 0, 2},   // 128 rows x 256 cells, 2 words x 2 rows per lane
     {8, 4, 8, 2, 0, 2},   // 256 rows x 256 cells, 2 words x 4 rows per lane
     {8, 8, 4, 4, 0},    // 128 rows x 256 cells, 4 warps of 8 rows per lane (fewer warps per barrier)
+    {8, 4, 4, 4, 0, 2},   // 128 rows x 256 cells, 4 warps of 2 words x 4 rows per lane
+    {8, 4, 3, 5, 0, 2},   //  96 rows x 256 cells, 3 warps of 2 words x 4 rows per lane
 };
 
 void *variant_fn(int v, int dist_bits) {
@@ -1131,6 +1133,8 @@ void *variant_fn(int v, int dist_bits) {
         case 9: return variant_ptr<8, 2, 8, 3, 2>(u16);
         case 10: return variant_ptr<8, 4, 8, 2, 2>(u16);
         case 11: return variant_ptr<8, 8, 4, 4>(u16);
+        case 12: return variant_ptr<8, 4, 4, 4, 2>(u16);
+        case 13: return variant_ptr<8, 4, 3, 5, 2>(u16);
         default: return nullptr;
     }
 }

@@ -375,8 +375,8 @@ typedef struct {
     int32_t graph;              /* 1: rounds replay a captured CUDA graph */
 } mpn_batch_stats_t;
 
-/* budget_bytes >= 1 MiB: the arena; variant: compiled tile shape 0 or 1
- * (-1 = 0); stream: cudaStream_t. */
+/* budget_bytes >= 1 MiB: the arena; variant: compiled tile shape 0, 1 or 12
+ * (-1 = 0; other shapes are MPN_EINVAL); stream: cudaStream_t. */
 mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream,
                             mpn_batch **out);
 

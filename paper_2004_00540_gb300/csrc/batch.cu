@@ -159,9 +159,9 @@ __global__ void k_batch_seed(BatchParams p, const SeedJob *jobs) {
 // whose 3 x 3 neighbourhood (within their grid) has finished the sweep. A
 // round's last sweep (the sweep budget) has no lookahead, so a round ends
 // with every visit of its sweeps done and nothing run ahead.
-template <int RXW, int R, int NW, int MINB>
+template <int RXW, int R, int NW, int MINB, int WPL = 1>
 __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p) {
-    __shared__ wave::VisitSmem<RXW, NW> sm;
+    __shared__ wave::VisitSmem<RXW, NW, WPL> sm;
     __shared__ int s_tile;
     __shared__ unsigned s_mask[2], s_lastj[2], s_done;
     __shared__ uint32_t s_len;   // length of this sweep's list
@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
         *fmask = 0u;
         *lastj = 0u;
         if (valid) {
-            if (with_hook) wave::visit_tile<RXW, R, NW>(v, sm, &p.descs[slot].err, fmask, lastj, wave::LogSink(), nullptr, hook);
-            else wave::visit_tile<RXW, R, NW>(v, sm, &p.descs[slot].err, fmask, lastj);
+            if (with_hook) wave::visit_tile<RXW, R, NW, WPL>(v, sm, &p.descs[slot].err, fmask, lastj, wave::LogSink(), nullptr, hook);
+            else wave::visit_tile<RXW, R, NW, WPL>(v, sm, &p.descs[slot].err, fmask, lastj);
         }
         if (maxl && v.l0 + (uint32_t)v.k >= maxl) *fmask = 0u;   // fixed depth reached
         *slot_out = slot;
@@ -508,17 +508,19 @@ __global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {
         p[i] = v;
 }
 
-template <int RXW, int R, int NW, int MINB>
+template <int RXW, int R, int NW, int MINB, int WPL = 1>
 void *batch_ptr() {
-    return (void *)k_batch_propagate<RXW, R, NW, MINB>;
+    return (void *)k_batch_propagate<RXW, R, NW, MINB, WPL>;
 }
 
-// The batch runs on compiled shape 0 (128-row x 8-word region) and its
-// 256-row sibling; per grid only the depth varies.
+// The batch runs on compiled shape 0 (128-row x 8-word region), its 256-row
+// sibling 1, or shape 12 (the same region held by 4 warps of two words x four
+// rows per lane); per grid only the depth varies.
 void *batch_fn(int v) {
     switch (v) {
         case 0: return batch_ptr<8, 4, 8, 3>();
         case 1: return batch_ptr<8, 8, 8, 2>();
+        case 12: return batch_ptr<8, 4, 4, 4, 2>();
         default: return nullptr;
     }
 }

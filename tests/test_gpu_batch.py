@@ -27,9 +27,10 @@ def check(b, tk, w):
     assert np.array_equal(paths.cells, cells)
 
 
-def test_batch_all_at_once():
+@pytest.mark.parametrize("shape", [0, 1, 12])
+def test_batch_all_at_once(shape):
     ws = small_members(24)
-    with pkg.Batch(1 << 30) as b:
+    with pkg.Batch(1 << 30, variant=shape) as b:
         tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
         assert all(t is not None for t in tks)
         running, done = b.run(0)
@@ -54,11 +55,12 @@ def test_batch_wait_runs_rounds_until_done():
             check(b, tk, w)
 
 
-def test_batch_continuous_arrivals_and_short_rounds():
+@pytest.mark.parametrize("shape", [0, 12])
+def test_batch_continuous_arrivals_and_short_rounds(shape):
     ws = small_members(30, side_hi=400, base_seed=40)
     rng = np.random.default_rng(1)
     order = rng.permutation(len(ws))
-    with pkg.Batch(1 << 30) as b:
+    with pkg.Batch(1 << 30, variant=shape) as b:
         b.set_depth(16)
         tickets = {}
         pending = list(order)

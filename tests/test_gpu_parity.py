@@ -306,9 +306,16 @@ def test_workload_c4_members(i):
     assert_parity(w.mask, w.targets, w.starts, dist_bits=w.dist_bits)
 
 
-def test_workload_c5_huge_full():
+@pytest.mark.parametrize("tiling", [None, (12, 28), (0, 24)])
+def test_workload_c5_huge_full(tiling):
+    """The full 23170^2 grid: automatic tiling (shape 12, depth 28, the
+    tiling the benchmark times after autotuning), the same explicitly, and
+    shape 0 at depth 24."""
     w = synth.c5_huge()
-    stats = assert_parity(w.mask, w.targets, w.starts)
+    kw = {} if tiling is None else {"variant": tiling[0], "depth": tiling[1]}
+    stats = assert_parity(w.mask, w.targets, w.starts, **kw)
+    if tiling is None:
+        assert (stats["variant"], stats["depth"]) == (12, 28)
     assert stats["layers"] > 100
     # the activation log carried the distances (one entry per word and
     # visit that reached cells in it), and visits stopped early where stable

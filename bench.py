@@ -440,8 +440,10 @@ def run_batched(args, pkg, torch):
                torch.empty(max(w.starts.size for w in ws) + 1, dtype=torch.int64).pin_memory(),
                torch.empty(max(w.starts.size for w in ws) + 1, dtype=torch.int8).pin_memory())
     with pkg.Batch(budget) as b:
-        rep = serve(b, reqs, round_sweeps=64, staging=staging)
-    out["serve"] = dict(rep.summary(), lambda_per_s=lam, round_sweeps=64)
+        rep = serve(b, reqs, round_sweeps=64, staging=staging, max_round_sweeps=1024)
+    out["serve"] = dict(rep.summary(), lambda_per_s=lam, round_sweeps=64, max_round_sweeps=1024,
+                        note="rounds of 64 sweeps; while no request arrives each round doubles, "
+                             "up to 1024")
     out["speedup_vs_per_maze_plain"] = out["batched"]["mazes_per_s"] / out["per_maze_plain_launches"]["mazes_per_s"]
     out["speedup_vs_per_maze_persistent"] = out["batched"]["mazes_per_s"] / out["per_maze_persistent"]["mazes_per_s"]
     return out

@@ -37,6 +37,7 @@ class ServeReport:
     refused_admissions: int = 0                      # submit attempts that did not fit yet
     results: dict = field(default_factory=dict)      # request index -> Paths (if kept)
     failed: list = field(default_factory=list)
+    round_sweeps: list = field(default_factory=list)  # sweep budget of each round
 
     def summary(self) -> dict:
         lat = np.asarray(self.latencies) * 1e3
@@ -65,13 +66,18 @@ def _own(a):
 
 
 def serve(batch: Batch, requests: list, round_sweeps: int = 64, keep_results: bool = False,
-          clock=time.perf_counter, staging=None) -> ServeReport:
+          clock=time.perf_counter, staging=None, max_round_sweeps: int = 0) -> ServeReport:
     """Run every request through the batch as it arrives; returns latencies.
     staging: optional (cells, offsets, status) host buffers (page-locked is
     fastest), each large enough for any one response; every response is
     downloaded into them (and copied out when kept) instead of into freshly
-    allocated arrays."""
+    allocated arrays. max_round_sweeps > round_sweeps: while no request has
+    arrived since the last round, each round runs twice as many sweeps as the
+    one before, up to max_round_sweeps (fewer rounds, so less time between
+    them, for the grids that need many sweeps); an arrival brings the rounds
+    back to round_sweeps, so that it joins soon."""
     rep = ServeReport()
+    cur = round_sweeps
     order = sorted(range(len(requests)), key=lambda i: requests[i].arrival)
     waiting = collections.deque()
     in_flight = {}                 # ticket -> request index
@@ -79,9 +85,11 @@ def serve(batch: Batch, requests: list, round_sweeps: int = 64, keep_results: bo
     t0 = clock()
     while nxt < len(order) or waiting or in_flight:
         now = clock() - t0
+        arrived = False
         while nxt < len(order) and requests[order[nxt]].arrival <= now:
             waiting.append(order[nxt])
             nxt += 1
+            arrived = True
         while waiting:
             r = requests[waiting[0]]
             tk = batch.submit(r.mask, r.targets, r.starts, r.dist_bits)
@@ -90,8 +98,12 @@ def serve(batch: Batch, requests: list, round_sweeps: int = 64, keep_results: bo
                 break
             in_flight[tk] = waiting.popleft()
         if in_flight:
-            batch.run(round_sweeps)
+            if arrived or waiting or max_round_sweeps <= round_sweeps:
+                cur = round_sweeps
+            batch.run(cur)
             rep.rounds += 1
+            rep.round_sweeps.append(cur)
+            cur = min(2 * cur, max(max_round_sweeps, round_sweeps))
             for tk in list(in_flight):
                 st = batch.poll(tk)
                 if st == MPN_BATCH_PENDING:

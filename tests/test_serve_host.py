@@ -102,3 +102,25 @@ def test_failures_are_reported_and_released():
     assert rep.failed == [1]
     assert not b.held
     assert rep.summary()["failed"] == 1
+
+
+def test_rounds_grow_while_nothing_arrives():
+    clock = FakeClock()
+    b = FakeBatch(slots=4, clock=clock)
+    reqs = [req(2000, 0.0), req(64, 0.0035)]
+    rep = sv.serve(b, reqs, round_sweeps=64, clock=clock, max_round_sweeps=512)
+    # the long grid alone: 64, 128, 256, 512 sweeps; the second request arrives
+    # during the 512-sweep round and the next round is short again
+    assert rep.round_sweeps[:6] == [64, 128, 256, 512, 64, 128]
+    assert max(rep.round_sweeps) == 512
+    assert sum(rep.round_sweeps) >= 2000
+    assert sorted(b.released) == sorted(b.submitted)
+    # the late request finished in the round right after it arrived
+    assert abs(rep.latencies[0] - 0.0015) < 1e-9
+
+
+def test_fixed_rounds_by_default():
+    clock = FakeClock()
+    b = FakeBatch(slots=4, clock=clock)
+    rep = sv.serve(b, [req(1000, 0.0)], round_sweeps=64, clock=clock)
+    assert rep.round_sweeps == [64] * 16

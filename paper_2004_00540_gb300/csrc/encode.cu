@@ -79,9 +79,7 @@ __global__ void k_pack_flat(const uint8_t *__restrict__ mask, size_t n, uint32_t
 __global__ void k_pack_rows(const uint32_t *__restrict__ flat, size_t nwords, int H, int W, int P,
                             uint32_t *__restrict__ out) {
     const size_t total = (size_t)H * P;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int y = (int)(i / P), w = (int)(i % P);
+    auto word = [&](int y, int w) {
         uint32_t v = 0u;
         const int rem = W - w * 32;
         if (rem > 0) {
@@ -91,8 +89,20 @@ __global__ void k_pack_rows(const uint32_t *__restrict__ flat, size_t nwords, in
             v = __funnelshift_r(lo, hi, (uint32_t)(b & 31));
             if (rem < 32) v &= (1u << rem) - 1u;
         }
-        out[i] = v;
+        return v;
+    };
+    // 32-bit index arithmetic (the usual case) where i + the stride cannot wrap
+    if (total + (size_t)gridDim.x * blockDim.x <= 0xffffffffull) {
+        const uint32_t t32 = (uint32_t)total, up = (uint32_t)P;
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < t32; i += gridDim.x * blockDim.x) {
+            const uint32_t y = i / up;
+            out[i] = word((int)y, (int)(i - y * up));
+        }
+        return;
     }
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x)
+        out[i] = word((int)(i / P), (int)(i % P));
 }
 
 // Copy a caller's packed free-cell plane (any pitch) into the context's

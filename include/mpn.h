@@ -213,7 +213,7 @@ mpn_status mpn_trace(mpn_ctx *ctx, const uint32_t *starts, int32_t n, uint64_t *
  * 4-neighbour (left, right, up, down, in Eq. 1's order) with the largest
  * activity, i.e. distance d - 1; then drop every point whose neighbours on
  * the path are sqrt(2) apart. Eq. 1 does not say what happens when no
- * 4-neighbour is one step closer (the closer cell is diagonal); this build
+ * 4-neighbour is one step closer (the closer cell is diagonal); this library
  * steps to the first 4-neighbour at the same distance that is 4-adjacent to a
  * closer cell (the corner of the diagonal move), or, if both corners are
  * obstacles, takes the diagonal step. Straightening scans forward: P(t) is

@@ -401,12 +401,14 @@ def run_batched(args, pkg, torch):
                 off=torch.empty(int(off_at[-1]), dtype=torch.int64).pin_memory(),
                 status=torch.empty(int(off_at[-1]), dtype=torch.int8).pin_memory(),
                 cell_at=cell_at.tolist(), off_at=off_at.tolist())
-    dt, res, st, _ = batched_once()
+    runs = [batched_once() for _ in range(3)]        # the host-side download varies run to run
+    dt, res, st, _ = min(runs, key=lambda r: r[0])
     out["batched"] = {"mazes_per_s": len(ws) / dt, "seconds": dt, "rounds": st["rounds"],
                       "sweeps": st["sweeps"], "propagate_round_ms": st["last_round_ms"],
-                      "path_cells": int(sum(totals)),
-                      "note": "submit + one round to convergence + every grid's paths, offsets and "
-                              "status downloaded into page-locked host buffers"}
+                      "path_cells": int(sum(totals)), "scheduling": "per-grid sweep clocks",
+                      "seconds_each": [r[0] for r in runs],
+                      "note": "best of 3: submit + one round to convergence + every grid's paths, "
+                              "offsets and status downloaded into page-locked host buffers"}
 
     # per grid, one persistent launch each (same library, no batching)
     t0 = time.perf_counter()

@@ -383,6 +383,18 @@ mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream
 /* Temporal depth used for grids submitted from now on (1..32, 0 = default). */
 mpn_status mpn_batch_set_depth(mpn_batch *b, int32_t depth);
 
+/* Scheduling of a batch's rounds (no counterpart in the paper, which solves
+ * one grid at a time). 1 (the default): every grid keeps its own sweep
+ * clock; a grid's next sweep starts as soon as its own tiles of the current
+ * one are done, and sweeps of at most 64 tiles are taken before larger ones,
+ * so a grid that needs many sweeps of few tiles (a maze) does not wait for
+ * the sweeps of large grids; a round's sweep budget counts each grid's own
+ * sweeps. 0: all grids advance together, one sweep of every grid per sweep
+ * of the launch (blocks waiting at a sweep's end run ready tiles of the
+ * next). Results are the same bit for bit. Only while the batch holds no
+ * grid (else MPN_ESTATE); shape 0, 1 or 12. */
+mpn_status mpn_batch_set_mode(mpn_batch *b, int32_t per_grid_clock);
+
 /* Admit one grid. dist_bits as in mpn_create; max_layers as in
  * mpn_propagate. *ticket identifies it. MPN_ENOMEM: it does not fit now.
  * End-points are checked here (the call waits for that): a target or start

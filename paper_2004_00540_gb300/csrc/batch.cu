@@ -44,12 +44,33 @@ struct MazeDesc {
     uint32_t last_push;     // 1 + last sweep one of its tiles was queued for
     uint32_t err;           // ERR_* bits of this grid
     uint32_t pad;
+    // per-grid sweep clock (the batch's per-grid mode)
+    uint32_t ls;            // the grid's sweep in progress, or the next one to run
+    uint32_t pend;          // visits of sweep ls not finished yet
+    uint32_t cnt[2];        // tiles queued in its list slot q (sweep parity q)
+    uint32_t ls0;           // ls when the round started
+    uint32_t fstate;        // kFlowIdle / kFlowReady / kFlowRun / kFlowDone
+};
+
+constexpr uint32_t kFlowIdle = 0, kFlowReady = 1, kFlowRun = 2, kFlowDone = 3;
+// a sweep of at most this many tiles goes to the priority ring
+constexpr uint32_t kFlowSmall = 64;
+
+// A counter alone in its 128-byte line (the per-grid mode's counters are
+// polled by idle blocks; sharing a line would slow every claim).
+struct alignas(128) LineWord {
+    uint32_t v;
+    uint32_t pad[31];
 };
 
 struct BatchCtl {
     Ctl c;
     uint32_t next_sweep;    // global sweep the next round starts at
     uint32_t pad[3];
+    // per-grid mode: two ticket rings (0: sweeps of few tiles, taken first)
+    LineWord head[2];       // tickets claimed
+    LineWord tail[2];       // tickets reserved by their publishers
+    LineWord active;        // grids of the round neither converged nor paused
 };
 
 struct BatchParams {
@@ -64,6 +85,8 @@ struct BatchParams {
     uint32_t spin_limit;
     uint32_t lookahead;     // 1: blocks waiting at a sweep's end run ready tiles of the next
     uint32_t *rank;         // kRankWords counters, zero at the launch (block ranks)
+    uint32_t *ring;         // per-grid mode: 2 rings of ring_mask + 1 tickets (1 + global tile id)
+    uint32_t ring_mask;
 };
 
 struct SeedJob {
@@ -122,9 +145,22 @@ __device__ void push_zone_b(const BatchParams &p, const MazeDesc &d, uint32_t sl
     if (zone & FB_SE) push_tile_b(p, d, slot, ty + 1, tx + 1, s);
 }
 
+// Per-grid mode: queue global tile gt of grid `slot` for the grid's sweep s
+// in the grid's own list slot s mod 2 (entries from tile_base on; a tile is
+// queued at most once per sweep, so the grid's tile count bounds the list).
+__device__ __forceinline__ void push_flow(const BatchParams &p, uint32_t slot, uint32_t gt, uint32_t s) {
+    if (atomicMax(p.stamps + gt, s + 1u) < s + 1u) {
+        MazeDesc &d = p.descs[slot];
+        const uint32_t q = s & 1u;
+        const uint32_t i = atomicAdd(&d.cnt[q], 1u);
+        wave::st_relaxed(p.lists + (size_t)q * p.max_tiles + d.tile_base + i, gt + 1u);
+    }
+}
+
 // One block per admitted grid: distance 0 and the reached bit at its
-// targets, and its first tiles queued for the round's first sweep.
-__global__ void k_batch_seed(BatchParams p, const SeedJob *jobs) {
+// targets, and its first tiles queued for the round's first sweep (per-grid
+// mode: for the grid's own sweep 0).
+__global__ void k_batch_seed(BatchParams p, const SeedJob *jobs, uint32_t flow) {
     const SeedJob job = jobs[blockIdx.x];
     const MazeDesc d = p.descs[job.slot];
     const uint32_t S = d.start_sweep;
@@ -147,7 +183,16 @@ __global__ void k_batch_seed(BatchParams p, const SeedJob *jobs) {
         atomicOr(d.g.state + 4 * wo + 2, bit);
         const int ty = y / d.TY, tx = (x >> 5) / d.TXW;
         const int ri = y - ty * d.TY, wi = (x >> 5) - tx * d.TXW;
-        push_zone_b(p, d, job.slot, ty, tx, wave::border_bits(ri, wi, bit, d.k, d.TY, d.TXW), S);
+        const uint32_t zone = wave::border_bits(ri, wi, bit, d.k, d.TY, d.TXW);
+        if (!flow) {
+            push_zone_b(p, d, job.slot, ty, tx, zone, S);
+            continue;
+        }
+        for (int z = 0; z < 9; ++z) {
+            if (!(zone & (1u << z))) continue;
+            const int64_t gt = zone_tile_b(d, ty, tx, 1u << z);
+            if (gt >= 0) push_flow(p, job.slot, (uint32_t)gt, 0u);
+        }
     }
 }
 
@@ -473,6 +518,235 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
     }
 }
 
+// ---- per-grid mode: every grid keeps its own sweep clock ----
+//
+// A ticket is 1 + a global tile id. The tickets of a grid's sweep s are
+// published together once its sweep s - 1 has finished (by the block that
+// finished its last visit), into ring 0 if the sweep has at most kFlowSmall
+// tiles, else ring 1; blocks take ring 0 first. So a grid never waits for
+// another grid's sweep, and a grid with few tiles per sweep (a maze) is not
+// queued behind the many tiles of a large one. Exactness is the same as with
+// one clock for all grids: a sweep's visits read their halos as of the start
+// of the sweep (parity of the grid's own sweep), and no visit of sweep s + 1
+// of a grid starts before every visit of its sweep s has finished.
+
+// Thread 0: claim a ticket; the global tile id, -1 once no grid of the round
+// is active (then no ticket is out), -2 after a wait ran out (recorded). A
+// claim is a fetch-and-add on the ring's head, taken only when the ring holds
+// unclaimed tickets; a block that lost the race for the last of them keeps
+// its index and waits for the ring's next publication to fill it (or for the
+// round to end: no grid active and the index past the ring's final tail).
+__device__ __forceinline__ uint64_t flow_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ int flow_claim(const BatchParams &p, BatchCtl *bc, unsigned spin_limit) {
+    unsigned spins = 0, nap = 32;
+    const uint64_t idle0 = flow_ns();
+    for (;;) {
+        for (int r = 0; r < 2; ++r) {
+            if (ld_relaxed(&bc->head[r].v) >= ld_acquire(&bc->tail[r].v)) continue;
+            const uint32_t h = atomicAdd(&bc->head[r].v, 1u);
+            uint32_t *e = p.ring + (size_t)r * (p.ring_mask + 1u) + (h & p.ring_mask);
+            const uint64_t t0 = flow_ns();
+            for (unsigned w = 1;; ++w) {
+                const uint32_t v = ld_acquire(e);
+                if (v) {
+                    wave::st_relaxed(e, 0u);
+                    return (int)(v - 1u);
+                }
+                if ((w & 15u) == 0u) {
+                    if (ld_acquire(&bc->active.v) == 0u && ld_acquire(&bc->tail[r].v) <= h) return -1;
+                    if (ld_acquire(&bc->c.err) & ERR_TIMEOUT) return -2;
+                    if (flow_ns() - t0 > 30000000000ull) {   // 30 s
+                        atomicOr(&bc->c.err, ERR_TIMEOUT);
+                        return -2;
+                    }
+                }
+                __nanosleep(w < 16 ? 32 : 256);
+            }
+        }
+        ++spins;
+        if ((spins & 7u) == 0u && ld_acquire(&bc->active.v) == 0u) return -1;
+        if ((spins & 63u) == 0u) {
+            if (ld_acquire(&bc->c.err) & ERR_TIMEOUT) return -2;
+            // no ticket for 30 s: record it and stop
+            if (flow_ns() - idle0 > 30000000000ull) {
+                atomicOr(&bc->c.err, ERR_TIMEOUT);
+                return -2;
+            }
+        }
+        __nanosleep(nap);   // idle: poll less often the longer nothing comes
+        if (nap < 512) nap *= 2;
+    }
+}
+
+// Store ticket `v` at index `i` of ring r once the slot's previous ticket has
+// been taken (bounded wait; false after spin_limit polls, recorded).
+__device__ __forceinline__ bool flow_put(const BatchParams &p, BatchCtl *bc, uint32_t r, uint32_t i,
+                                         uint32_t v, unsigned spin_limit) {
+    uint32_t *e = p.ring + (size_t)r * (p.ring_mask + 1u) + (i & p.ring_mask);
+    unsigned w = 0;
+    while (ld_acquire(e) != 0u) {
+        if (++w > spin_limit) {
+            atomicOr(&bc->c.err, ERR_TIMEOUT);
+            return false;
+        }
+        if (w > 8) __nanosleep(32);
+    }
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(e), "r"(v) : "memory");
+    return true;
+}
+
+template <int RXW, int R, int NW, int MINB, int WPL = 1>
+__global__ void __launch_bounds__(NW * 32, MINB) k_batch_flow(BatchParams p) {
+    __shared__ wave::VisitSmem<RXW, NW, WPL> sm;
+    __shared__ int s_tile;
+    __shared__ unsigned s_mask, s_lastj;
+    __shared__ uint32_t s_pub_n, s_pub_base, s_pub_r;
+    BatchCtl *bc = p.bc;
+    Ctl *ctl = &bc->c;
+    const size_t MT = p.max_tiles;
+    unsigned long long blk_visits = 0;
+    sm.zero_pad();   // (the first barrier below publishes it)
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_mask = 0u;
+            s_lastj = 0u;
+            s_tile = flow_claim(p, bc, p.spin_limit);
+        }
+        __syncthreads();
+        const int t = s_tile;
+        if (t < 0) break;   // block-uniform
+        // ---- one visit of tile t at its grid's current sweep ----
+        const uint32_t slot = __ldg(p.tile_maze + t);
+        MazeDesc &dref = p.descs[slot];
+        const uint32_t ls = ld_relaxed(&dref.ls);   // fixed while this sweep's tickets are out
+        wave::Visit v;
+        v.g = dref.g;
+        v.dist_bits = dref.dist_bits;
+        v.TY = dref.TY;
+        v.TXW = dref.TXW;
+        v.k = dref.k;
+        const uint32_t local = (uint32_t)t - dref.tile_base;
+        const bool valid = local < (uint32_t)(dref.ntx * dref.nty);   // defensive
+        v.ty = (int)(local / (uint32_t)dref.ntx);
+        v.tx = (int)(local - (uint32_t)v.ty * dref.ntx);
+        v.l0 = ls * (uint32_t)v.k;
+        const uint32_t maxl = dref.max_layers;
+        v.jmax = v.k;
+        if (maxl && v.l0 + (uint32_t)v.k > maxl) v.jmax = (int)(maxl - v.l0);
+        v.par = (int)(ls & 1u);
+        uint32_t fmask = 0u;
+        unsigned lastj = 0u;
+        if (valid) wave::visit_tile<RXW, R, NW, WPL>(v, sm, &dref.err, &fmask, &lastj);
+        if (maxl && v.l0 + (uint32_t)v.k >= maxl) fmask = 0u;   // fixed depth reached
+        if (fmask) atomicOr(&s_mask, fmask);
+        if (lastj) atomicMax(&s_lastj, lastj);
+        if (threadIdx.x == 0) ++blk_visits;
+        __syncthreads();
+        // ---- the tiles it reaches, queued for the grid's sweep ls + 1: lanes
+        // 0..8 of warp 0 (one border zone each), one count-up for all ----
+        if (threadIdx.x < 32) {
+            const uint32_t zone = 1u << threadIdx.x;
+            int64_t gt = -1;
+            if (threadIdx.x < 9 && (s_mask & zone)) gt = zone_tile_b(dref, v.ty, v.tx, zone);
+            const bool fresh = gt >= 0 && atomicMax(p.stamps + gt, ls + 2u) < ls + 2u;
+            const unsigned fm = __ballot_sync(0xffffffffu, fresh);
+            if (fm) {
+                const int lead = __ffs(fm) - 1;
+                const uint32_t q1 = (ls + 1u) & 1u;
+                uint32_t base = 0u;
+                if ((int)threadIdx.x == lead) base = atomicAdd(&dref.cnt[q1], (uint32_t)__popc(fm));
+                base = __shfl_sync(0xffffffffu, base, lead);
+                if (fresh)
+                    wave::st_relaxed(p.lists + (size_t)q1 * MT + dref.tile_base + base +
+                                         (uint32_t)__popc(fm & ((1u << threadIdx.x) - 1u)),
+                                     (uint32_t)gt + 1u);
+            }
+            if (threadIdx.x == 0 && s_lastj) atomicMax(&dref.maxl, v.l0 + s_lastj);
+        }
+        __syncthreads();   // the visit's writes and pushes come before the count-down
+        // ---- count down the grid's sweep; the last visit moves the grid on ----
+        if (threadIdx.x == 0) {
+            s_pub_n = 0u;
+            uint32_t old;
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                         : "=r"(old) : "l"(&dref.pend), "r"(0xffffffffu) : "memory");
+            if (old == 1u) {
+                const uint32_t q1 = (ls + 1u) & 1u;
+                const uint32_t n = ld_relaxed(&dref.cnt[q1]);
+                const uint32_t ran = ls + 1u - dref.ls0;
+                atomicMax(&ctl->sweeps, ran);
+                if (n == 0u || (p.round_sweeps && ran >= p.round_sweeps)) {
+                    // converged, or paused at the round's sweep budget (its
+                    // next sweep's list is published by the next round)
+                    dref.ls = ls + 1u;
+                    dref.fstate = n == 0u ? kFlowDone : kFlowReady;
+                    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&bc->active.v),
+                                 "r"(0xffffffffu) : "memory");
+                } else {
+                    dref.ls = ls + 1u;
+                    dref.pend = n;
+                    dref.cnt[q1] = 0u;   // (the entries stay; slot q1 serves sweep ls + 3 next)
+                    const uint32_t r = n <= kFlowSmall ? 0u : 1u;
+                    s_pub_base = atomicAdd(&bc->tail[r].v, n);
+                    s_pub_r = r;
+                    s_pub_n = n;
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t pn = s_pub_n;
+        if (pn) {   // block-uniform: publish sweep ls + 1's tickets
+            const uint32_t q1 = (ls + 1u) & 1u;
+            const uint32_t *lst = p.lists + (size_t)q1 * MT + dref.tile_base;
+            for (uint32_t i = threadIdx.x; i < pn; i += blockDim.x)
+                if (!flow_put(p, bc, s_pub_r, s_pub_base + i, ld_relaxed(lst + i), p.spin_limit)) break;
+        }
+    }
+    if (threadIdx.x == 0 && blk_visits) atomicAdd(&ctl->visits, blk_visits);
+}
+
+// Per-grid mode, round preparation: fresh rings and counters ...
+__global__ void k_flow_reset(BatchCtl *bc) {
+    bc->c.err = 0u;
+    bc->c.sweeps = 0u;
+    bc->head[0].v = bc->head[1].v = 0u;
+    bc->tail[0].v = bc->tail[1].v = 0u;
+    bc->active.v = 0u;
+}
+
+// ... then, one warp per grid slot, the first sweep of every grid that is
+// ready (new, or paused at the last round's budget) published.
+__global__ void k_flow_prep(BatchParams p, uint32_t nslots) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (slot >= nslots) return;
+    MazeDesc &d = p.descs[slot];
+    if (d.fstate != kFlowReady) return;   // warp-uniform
+    const uint32_t q = d.ls & 1u, n = d.cnt[q];
+    uint32_t base = 0u, r = n <= kFlowSmall ? 0u : 1u;
+    if (lane == 0) {
+        if (n) {
+            base = atomicAdd(&p.bc->tail[r].v, n);
+            d.pend = n;
+            d.cnt[q] = 0u;
+            d.ls0 = d.ls;
+            d.fstate = kFlowRun;
+            atomicAdd(&p.bc->active.v, 1u);
+        } else {
+            d.fstate = kFlowDone;   // (a grid always has its targets' tiles queued)
+        }
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const uint32_t *lst = p.lists + (size_t)q * p.max_tiles + d.tile_base;
+    uint32_t *ring = p.ring + (size_t)r * (p.ring_mask + 1u);
+    for (uint32_t i = lane; i < n; i += 32) ring[(base + i) & p.ring_mask] = lst[i];
+}
+
 // Submit-time check: every target in range and on a free cell, every start
 // in range (bit 0: target out of range, 1: target on an obstacle, 2: start
 // out of range).
@@ -511,6 +785,20 @@ __global__ void k_fill_u32(uint32_t *p, uint32_t n, uint32_t v) {
 template <int RXW, int R, int NW, int MINB, int WPL = 1>
 void *batch_ptr() {
     return (void *)k_batch_propagate<RXW, R, NW, MINB, WPL>;
+}
+
+template <int RXW, int R, int NW, int MINB, int WPL = 1>
+void *flow_ptr() {
+    return (void *)k_batch_flow<RXW, R, NW, MINB, WPL>;
+}
+
+void *flow_fn(int v) {
+    switch (v) {
+        case 0: return flow_ptr<8, 4, 8, 3>();
+        case 1: return flow_ptr<8, 8, 8, 2>();
+        case 12: return flow_ptr<8, 4, 4, 4, 2>();
+        default: return nullptr;
+    }
 }
 
 // The batch runs on compiled shape 0 (128-row x 8-word region), its 256-row
@@ -639,8 +927,13 @@ struct mpn_batch {
     size_t jump_cells = 0;
     BatchSeg *d_segs = nullptr;   // followed by the segment counter
     size_t seg_cap = 0;
-    std::map<uint64_t, cudaGraphExec_t> graphs;   // one captured round per (max_sweeps, lookahead)
+    std::map<uint64_t, cudaGraphExec_t> graphs;   // one captured round per (max_sweeps, mode, lookahead)
     bool use_graph = true;
+    // per-grid mode (mpn_batch_set_mode): every grid keeps its own sweep clock
+    bool flow = false;
+    int flow_blocks = 0;
+    uint32_t *d_ring = nullptr;   // two ticket rings
+    uint32_t ring_mask = 0;
     float last_round_ms = 0.f;
     uint64_t rounds = 0, sweeps_total = 0;
 };
@@ -753,7 +1046,42 @@ mpn_status mpn_batch_create(uint64_t budget_bytes, int32_t variant, void *stream
     b->mem.init(budget_bytes);
     b->tiles.init(b->max_tiles);
     for (uint32_t i = b->max_slots; i-- > 0;) b->free_slots.push_back(i);
+    // per-grid sweep clocks by default (the shape has that kernel)
+    if (flow_fn(variant)) {
+        const mpn_status ms = mpn_batch_set_mode(b, 1);
+        if (ms != MPN_OK) {
+            mpn_batch_destroy(b);
+            return ms;
+        }
+    }
     *out = b;
+    return MPN_OK;
+}
+
+mpn_status mpn_batch_set_mode(mpn_batch *b, int32_t per_grid_clock) {
+    if (!b || (per_grid_clock != 0 && per_grid_clock != 1)) return MPN_EINVAL;
+    if (!b->mazes.empty()) return MPN_ESTATE;   // only while the batch holds no grid
+    if (!per_grid_clock) {
+        b->flow = false;
+        return MPN_OK;
+    }
+    void *fn = flow_fn(b->variant);
+    if (!fn) return MPN_EINVAL;
+    const VariantDesc vd = variant_desc(b->variant);
+    int bps = 0;
+    B_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, vd.nwarps * 32, 0));
+    if (bps < 1) return MPN_ECUDA;
+    if (!b->d_ring) {
+        // each ring holds every tile of the batch once plus a claim per block
+        size_t n = 1;
+        while (n < (size_t)b->max_tiles + (size_t)bps * b->sm_count + 1) n <<= 1;
+        B_TRY(cudaMalloc((void **)&b->d_ring, 2 * n * sizeof(uint32_t)));
+        B_TRY(cudaMemsetAsync(b->d_ring, 0, 2 * n * sizeof(uint32_t), b->stream));
+        B_TRY(cudaStreamSynchronize(b->stream));
+        b->ring_mask = (uint32_t)(n - 1);
+    }
+    b->flow_blocks = bps * b->sm_count;
+    b->flow = true;
     return MPN_OK;
 }
 
@@ -865,9 +1193,19 @@ mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_
 // The round: device-side preparation, then the cooperative persistent launch.
 static cudaError_t enqueue_round(mpn_batch *b, const BatchParams &p) {
     cudaStream_t st = b->stream;
-    k_round_prep<<<1, 1, 0, st>>>(b->d_bc);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    if (b->flow) {   // fresh rings, then every ready grid's first sweep published
+        k_flow_reset<<<1, 1, 0, st>>>(b->d_bc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_flow_prep<<<(b->max_slots + 7) / 8, 256, 0, st>>>(p, b->max_slots);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    } else {
+        k_round_prep<<<1, 1, 0, st>>>(b->d_bc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     e = cudaMemsetAsync(b->d_rank, 0, kRankWords * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     // external records, so that they time the round also when it is captured
@@ -875,7 +1213,7 @@ static cudaError_t enqueue_round(mpn_batch *b, const BatchParams &p) {
     if (e != cudaSuccess) return e;
     const VariantDesc vd = variant_desc(b->variant);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(b->blocks);
+    cfg.gridDim = dim3(b->flow ? b->flow_blocks : b->blocks);
     cfg.blockDim = dim3(vd.nwarps * 32);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
@@ -886,7 +1224,7 @@ static cudaError_t enqueue_round(mpn_batch *b, const BatchParams &p) {
     cfg.numAttrs = 1;
     BatchParams pp = p;
     void *args[] = {&pp};
-    e = cudaLaunchKernelExC(&cfg, batch_fn(b->variant), args);
+    e = cudaLaunchKernelExC(&cfg, b->flow ? flow_fn(b->variant) : batch_fn(b->variant), args);
     if (e != cudaSuccess) return e;
     return cudaEventRecordWithFlags(b->ev1, st, cudaEventRecordExternal);
 }
@@ -899,7 +1237,7 @@ static cudaError_t run_round(mpn_batch *b, const BatchParams &p) {
         count_launch(2);
         return enqueue_round(b, p);
     }
-    const uint64_t key = ((uint64_t)p.round_sweeps << 1) | (p.lookahead & 1u);
+    const uint64_t key = ((uint64_t)p.round_sweeps << 2) | ((uint64_t)b->flow << 1) | (p.lookahead & 1u);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         cudaStream_t cs = nullptr;
@@ -956,13 +1294,18 @@ static mpn_status finish_round(mpn_batch *b) {
                           cudaMemcpyDeviceToHost, st));
     B_TRY(cudaStreamSynchronize(st));
     b->next_sweep = b->h_bc->next_sweep;
-    if (b->h_bc->c.err & ERR_TIMEOUT) return MPN_ETIMEOUT;
+    if (b->h_bc->c.err & ERR_TIMEOUT) {
+        // (per-grid mode: tickets may be left in the rings; start them empty)
+        if (b->flow) cudaMemsetAsync(b->d_ring, 0, 2 * ((size_t)b->ring_mask + 1) * sizeof(uint32_t), st);
+        return MPN_ETIMEOUT;
+    }
     std::vector<HostMaze *> done;
     for (auto &kv : b->mazes) {
         HostMaze &m = kv.second;
         if (m.state != MState::Running) continue;
         const MazeDesc &d = b->h_descs[m.slot];
-        if (d.last_push > b->next_sweep) continue;   // tiles still queued for the next sweep
+        if (b->flow ? d.fstate != kFlowDone                    // per-grid mode: not converged yet
+                    : d.last_push > b->next_sweep) continue;   // tiles still queued for the next sweep
         if (d.err) {
             // (a uint16 overflow; end-points were checked at submit) -- the grid
             // has drained, so its planes can go
@@ -1118,6 +1461,7 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, 
         d.tile_base = m.tile_base;
         d.start_sweep = b->next_sweep;
         d.max_layers = m.max_layers;
+        d.fstate = b->flow ? kFlowReady : kFlowIdle;   // (ls, pend, cnt start at zero)
         b->h_descs[m.slot] = d;
         B_TRY(cudaMemcpyAsync(b->d_descs + m.slot, &b->h_descs[m.slot], sizeof(MazeDesc),
                               cudaMemcpyHostToDevice, st));
@@ -1153,6 +1497,8 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, 
     p.max_tiles = b->max_tiles;
     p.bc = b->d_bc;
     p.rank = b->d_rank;
+    p.ring = b->d_ring;
+    p.ring_mask = b->ring_mask;
     p.round_sweeps = max_sweeps;
     p.spin_limit = 1u << 24;
     p.lookahead = 1;
@@ -1161,7 +1507,7 @@ mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running, 
     if (njobs > 0) {
         B_TRY(cudaMemcpyAsync(b->d_jobs, b->h_jobs, njobs * sizeof(SeedJob), cudaMemcpyHostToDevice, st));
         count_launch();
-        k_batch_seed<<<njobs, 128, 0, st>>>(p, b->d_jobs);
+        k_batch_seed<<<njobs, 128, 0, st>>>(p, b->d_jobs, b->flow ? 1u : 0u);
         B_TRY(cudaGetLastError());
     }
     int running = 0;
@@ -1321,6 +1667,7 @@ void mpn_batch_destroy(mpn_batch *b) {
     cudaFree(b->d_lists);
     cudaFree(b->d_bc);
     cudaFree(b->d_rank);
+    cudaFree(b->d_ring);
     cudaFree(b->d_jobs);
     if (b->h_descs) cudaFreeHost(b->h_descs);
     if (b->h_bc) cudaFreeHost(b->h_bc);

@@ -29,7 +29,7 @@ EXPORTS = (
     "mpn_propagate_plain", "mpn_get_distances", "mpn_get_distances_async", "mpn_get_activity",
     "mpn_trace_lengths", "mpn_trace", "mpn_sync", "mpn_destroy", "mpn_status_str", "mpn_set_tuning",
     "mpn_variant_info", "mpn_get_stats", "mpn_launch_count", "mpn_propagate_noalloc",
-    "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_submit", "mpn_batch_run",
+    "mpn_batch_create", "mpn_batch_set_depth", "mpn_batch_set_mode", "mpn_batch_submit", "mpn_batch_run",
     "mpn_batch_poll", "mpn_batch_wait", "mpn_batch_result", "mpn_batch_info", "mpn_batch_release",
     "mpn_batch_stats", "mpn_batch_destroy", "mpn_autotune", "mpn_trace_euclid",
     "mpn_nearest_targets", "mpn_last_error", "mpn_tune_query", "mpn_propagate_resume", "mpn_check",
@@ -119,6 +119,7 @@ def load(path: str = LIB_PATH, build_if_missing: bool = True):
             "mpn_propagate_noalloc": ([vp, i32, i32, vp, i32, u32, vp, vp], ctypes.c_int),
             "mpn_batch_create": ([u64, i32, vp, pp], ctypes.c_int),
             "mpn_batch_set_depth": ([vp, i32], ctypes.c_int),
+            "mpn_batch_set_mode": ([vp, i32], ctypes.c_int),
             "mpn_batch_submit": ([vp, vp, i32, i32, vp, i32, vp, i32, i32, u32,
                                   ctypes.POINTER(u64)], ctypes.c_int),
             "mpn_batch_run": ([vp, u32, ctypes.POINTER(i32), ctypes.POINTER(i32)], ctypes.c_int),
@@ -516,6 +517,10 @@ class Batch:
 
     def set_depth(self, depth: int):
         _check(load().mpn_batch_set_depth(self.h, depth), "mpn_batch_set_depth")
+
+    def set_mode(self, per_grid_clock: bool):
+        """True: every grid keeps its own sweep clock (see include/mpn.h)."""
+        _check(load().mpn_batch_set_mode(self.h, 1 if per_grid_clock else 0), "mpn_batch_set_mode")
 
     def submit(self, mask, targets, starts, dist_bits: int = MPN_DIST_AUTO, max_layers: int = 0):
         """Ticket, or None when the grid does not fit in the arena now."""

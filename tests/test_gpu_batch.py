@@ -27,10 +27,12 @@ def check(b, tk, w):
     assert np.array_equal(paths.cells, cells)
 
 
+@pytest.mark.parametrize("per_grid", [False, True])
 @pytest.mark.parametrize("shape", [0, 1, 12])
-def test_batch_all_at_once(shape):
+def test_batch_all_at_once(shape, per_grid):
     ws = small_members(24)
     with pkg.Batch(1 << 30, variant=shape) as b:
+        b.set_mode(per_grid)
         tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
         assert all(t is not None for t in tks)
         running, done = b.run(0)
@@ -42,9 +44,11 @@ def test_batch_all_at_once(shape):
         assert b.stats()["arena_used"] == 0
 
 
-def test_batch_wait_runs_rounds_until_done():
+@pytest.mark.parametrize("per_grid", [False, True])
+def test_batch_wait_runs_rounds_until_done(per_grid):
     ws = small_members(6, side_hi=260, base_seed=60)
     with pkg.Batch(1 << 30) as b:
+        b.set_mode(per_grid)
         tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
         # short rounds: the wait takes several of them; the others advance too
         assert b.wait(tks[3], 2) == pkg.MPN_BATCH_DONE
@@ -55,12 +59,14 @@ def test_batch_wait_runs_rounds_until_done():
             check(b, tk, w)
 
 
+@pytest.mark.parametrize("per_grid", [False, True])
 @pytest.mark.parametrize("shape", [0, 12])
-def test_batch_continuous_arrivals_and_short_rounds(shape):
+def test_batch_continuous_arrivals_and_short_rounds(shape, per_grid):
     ws = small_members(30, side_hi=400, base_seed=40)
     rng = np.random.default_rng(1)
     order = rng.permutation(len(ws))
     with pkg.Batch(1 << 30, variant=shape) as b:
+        b.set_mode(per_grid)
         b.set_depth(16)
         tickets = {}
         pending = list(order)
@@ -122,9 +128,11 @@ def test_batch_rejects_bad_endpoints_and_overflow_fails_alone():
             check(b, tk, w)
 
 
-def test_batch_fixed_depth():
+@pytest.mark.parametrize("per_grid", [False, True])
+def test_batch_fixed_depth(per_grid):
     w = synth.c4_member(2, 4, 64, 300)
     with pkg.Batch(1 << 28) as b:
+        b.set_mode(per_grid)
         tk = b.submit(w.mask, w.targets, w.starts, w.dist_bits, max_layers=9)
         b.run(0)
         dist, paths, layers = b.result(tk, w.starts.size)
@@ -132,16 +140,19 @@ def test_batch_fixed_depth():
     assert np.array_equal(widen(dist), od) and layers == oL
 
 
-def test_batch_full_size_members_sample():
+@pytest.mark.parametrize("per_grid", [False, True])
+def test_batch_full_size_members_sample(per_grid):
     ws = [synth.c4_member(i) for i in (0, 1, 2, 3, 101, 254, 255)]
     with pkg.Batch(16 << 30) as b:
+        b.set_mode(per_grid)
         tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
         b.run(0)
         for tk, w in zip(tks, ws):
             check(b, tk, w)
 
 
-def test_serve_on_the_real_engine_matches_oracle_alone_and_in_the_mix():
+@pytest.mark.parametrize("per_grid", [False, True])
+def test_serve_on_the_real_engine_matches_oracle_alone_and_in_the_mix(per_grid):
     """The continuous-batching loop (serve) on the real batched engine:
     Poisson arrivals, rounds of a few sweeps so that requests arriving while
     others are on the GPU join later rounds, every served path kept. Each
@@ -152,7 +163,8 @@ def test_serve_on_the_real_engine_matches_oracle_alone_and_in_the_mix():
     arr = synth.poisson_arrivals(len(ws), 400.0, seed=3)
     reqs = [Request(w.mask, w.targets, w.starts, w.dist_bits, float(a)) for w, a in zip(ws, arr)]
     with pkg.Batch(1 << 30) as b:
-        rep = serve(b, reqs, round_sweeps=4, keep_results=True)
+        b.set_mode(per_grid)
+        rep = serve(b, reqs, round_sweeps=4, keep_results=True, max_round_sweeps=16)
         assert b.stats()["graph"] == 1
     assert not rep.failed and len(rep.results) == len(ws)
     assert rep.rounds > 3
@@ -178,6 +190,7 @@ def test_batch_without_lookahead_same_results(monkeypatch):
     ws = small_members(10, side_hi=420, base_seed=150)
     monkeypatch.setenv("MPN_TEST_NO_LOOKAHEAD", "1")
     with pkg.Batch(1 << 30) as b:
+        b.set_mode(False)             # the lookahead is the global-sweep mode's
         tks = [b.submit(w.mask, w.targets, w.starts, w.dist_bits) for w in ws]
         b.run(3)                      # a short round, then the rest
         b.run(0)
@@ -207,3 +220,19 @@ def test_batch_long_walks_in_segments():
         b.run(0)
         for tk, w in tks:
             check(b, tk, w)
+
+
+def test_batch_mode_only_while_empty():
+    w = synth.c4_member(2, 4, 64, 300)
+    with pkg.Batch(1 << 28) as b:
+        b.set_mode(True)
+        tk = b.submit(w.mask, w.targets, w.starts, w.dist_bits)
+        with pytest.raises(pkg.MPNError):
+            b.set_mode(False)                    # a grid is in the batch
+        b.run(0)
+        check(b, tk, w)
+        b.release(tk)
+        b.set_mode(False)                        # empty again
+        tk = b.submit(w.mask, w.targets, w.starts, w.dist_bits)
+        b.run(0)
+        check(b, tk, w)

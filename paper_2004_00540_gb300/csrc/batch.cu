@@ -71,6 +71,9 @@ struct BatchCtl {
     LineWord head[2];       // tickets claimed
     LineWord tail[2];       // tickets reserved by their publishers
     LineWord active;        // grids of the round neither converged nor paused
+    LineWord reached;       // grids of the round that ran the sweep budget (or converged first)
+    uint32_t round_grids;   // grids the round started with
+    uint32_t pad3[31];
 };
 
 struct BatchParams {
@@ -680,9 +683,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_flow(BatchParams p) {
                 const uint32_t n = ld_relaxed(&dref.cnt[q1]);
                 const uint32_t ran = ls + 1u - dref.ls0;
                 atomicMax(&ctl->sweeps, ran);
-                if (n == 0u || (p.round_sweeps && ran >= p.round_sweeps)) {
-                    // converged, or paused at the round's sweep budget (its
-                    // next sweep's list is published by the next round)
+                // with a sweep budget B: a grid counts as reached once it ran B
+                // sweeps (or converged before); it pauses once every grid of
+                // the round has reached B, or at 16 B -- so a grid of fast
+                // sweeps is not held to a slow grid's pace within the round
+                const uint32_t B = p.round_sweeps;
+                if (B && (ran == B || (n == 0u && ran < B))) atomicAdd(&bc->reached.v, 1u);
+                const bool pause = B && n != 0u &&
+                                   (ran >= 16u * B || (ran >= B && ld_acquire(&bc->reached.v) >= bc->round_grids));
+                if (n == 0u || pause) {
+                    // converged, or paused (its next sweep's list is
+                    // published by the next round)
                     dref.ls = ls + 1u;
                     dref.fstate = n == 0u ? kFlowDone : kFlowReady;
                     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&bc->active.v),
@@ -717,6 +728,8 @@ __global__ void k_flow_reset(BatchCtl *bc) {
     bc->head[0].v = bc->head[1].v = 0u;
     bc->tail[0].v = bc->tail[1].v = 0u;
     bc->active.v = 0u;
+    bc->reached.v = 0u;
+    bc->round_grids = 0u;
 }
 
 // ... then, one warp per grid slot, the first sweep of every grid that is
@@ -737,6 +750,7 @@ __global__ void k_flow_prep(BatchParams p, uint32_t nslots) {
             d.ls0 = d.ls;
             d.fstate = kFlowRun;
             atomicAdd(&p.bc->active.v, 1u);
+            atomicAdd(&p.bc->round_grids, 1u);
         } else {
             d.fstate = kFlowDone;   // (a grid always has its targets' tiles queued)
         }

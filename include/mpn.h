@@ -406,8 +406,13 @@ mpn_status mpn_batch_submit(mpn_batch *b, const uint8_t *mask, int32_t H, int32_
                             const uint32_t *starts, int32_t n_starts, int32_t dist_bits,
                             uint32_t max_layers, uint64_t *ticket);
 
-/* One round (waits for it). n_running: grids admitted or in flight after the
- * round; n_done: grids finished (done or failed) and not yet released. */
+/* One round (waits for it). max_sweeps: the round's sweep budget, 0 = until
+ * every grid converged. With one clock for all grids a round runs at most
+ * max_sweeps sweeps; with per-grid clocks every grid runs at least
+ * max_sweeps of its own sweeps (or converges), and one whose sweeps are
+ * faster runs on, up to 16 x max_sweeps, until every grid of the round has
+ * run max_sweeps. n_running: grids admitted or in flight after the round;
+ * n_done: grids finished (done or failed) and not yet released. */
 mpn_status mpn_batch_run(mpn_batch *b, uint32_t max_sweeps, int32_t *n_running,
                          int32_t *n_done);
 

@@ -533,19 +533,21 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_propagate(BatchParams p
 // of the sweep (parity of the grid's own sweep), and no visit of sweep s + 1
 // of a grid starts before every visit of its sweep s has finished.
 
-// Thread 0: claim a ticket; the global tile id, -1 once no grid of the round
-// is active (then no ticket is out), -2 after a wait ran out (recorded). A
-// claim is a fetch-and-add on the ring's head, taken only when the ring holds
-// unclaimed tickets; a block that lost the race for the last of them keeps
-// its index and waits for the ring's next publication to fill it (or for the
-// round to end: no grid active and the index past the ring's final tail).
 __device__ __forceinline__ uint64_t flow_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
 
-__device__ int flow_claim(const BatchParams &p, BatchCtl *bc, unsigned spin_limit) {
+// Thread 0: claim a ticket; the global tile id, -1 once no grid of the round
+// is active (then no ticket is out), -2 after a wait ran out (recorded). A
+// claim is a fetch-and-add on the ring's head, taken only when the ring holds
+// unclaimed tickets; a block that lost the race for the last of them keeps
+// its index and waits for the ring's next publication to fill it (or for the
+// round to end: no grid active and the index past the ring's final tail).
+// (A compare-and-swap claim lost most races under hundreds of claimers: one
+// winner per round trip.) Both waits end after 30 s of the global timer.
+__device__ int flow_claim(const BatchParams &p, BatchCtl *bc) {
     unsigned spins = 0, nap = 32;
     const uint64_t idle0 = flow_ns();
     for (;;) {
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_batch_flow(BatchParams p) {
         if (threadIdx.x == 0) {
             s_mask = 0u;
             s_lastj = 0u;
-            s_tile = flow_claim(p, bc, p.spin_limit);
+            s_tile = flow_claim(p, bc);
         }
         __syncthreads();
         const int t = s_tile;

@@ -546,16 +546,22 @@ __device__ __forceinline__ uint64_t flow_ns() {
 // its index and waits for the ring's next publication to fill it (or for the
 // round to end: no grid active and the index past the ring's final tail).
 // (A compare-and-swap claim lost most races under hundreds of claimers: one
-// winner per round trip.) Both waits end after 30 s of the global timer.
+// winner per round trip.) Both waits end after 30 s of the global timer in
+// which nothing was published.
 __device__ int flow_claim(const BatchParams &p, BatchCtl *bc) {
     unsigned spins = 0, nap = 32;
-    const uint64_t idle0 = flow_ns();
+    uint64_t idle0 = flow_ns();
+    uint32_t seen = 0xffffffffu;   // tails last seen (their sum grows with every publication)
     for (;;) {
+        uint32_t tsum = 0u;
         for (int r = 0; r < 2; ++r) {
-            if (ld_relaxed(&bc->head[r].v) >= ld_acquire(&bc->tail[r].v)) continue;
+            const uint32_t t = ld_acquire(&bc->tail[r].v);
+            tsum += t;
+            if (ld_relaxed(&bc->head[r].v) >= t) continue;
             const uint32_t h = atomicAdd(&bc->head[r].v, 1u);
             uint32_t *e = p.ring + (size_t)r * (p.ring_mask + 1u) + (h & p.ring_mask);
-            const uint64_t t0 = flow_ns();
+            uint64_t t0 = flow_ns();
+            uint32_t seen_r = t;
             for (unsigned w = 1;; ++w) {
                 const uint32_t v = ld_acquire(e);
                 if (v) {
@@ -563,9 +569,13 @@ __device__ int flow_claim(const BatchParams &p, BatchCtl *bc) {
                     return (int)(v - 1u);
                 }
                 if ((w & 15u) == 0u) {
-                    if (ld_acquire(&bc->active.v) == 0u && ld_acquire(&bc->tail[r].v) <= h) return -1;
+                    const uint32_t tr = ld_acquire(&bc->tail[r].v);
+                    if (ld_acquire(&bc->active.v) == 0u && tr <= h) return -1;
                     if (ld_acquire(&bc->c.err) & ERR_TIMEOUT) return -2;
-                    if (flow_ns() - t0 > 30000000000ull) {   // 30 s
+                    if (tr != seen_r) {   // the ring moves on: the wait is not stuck
+                        seen_r = tr;
+                        t0 = flow_ns();
+                    } else if (flow_ns() - t0 > 30000000000ull) {   // 30 s without a publication
                         atomicOr(&bc->c.err, ERR_TIMEOUT);
                         return -2;
                     }
@@ -575,10 +585,13 @@ __device__ int flow_claim(const BatchParams &p, BatchCtl *bc) {
         }
         ++spins;
         if ((spins & 7u) == 0u && ld_acquire(&bc->active.v) == 0u) return -1;
+        if (tsum != seen) {   // something was published since the last look
+            seen = tsum;
+            idle0 = flow_ns();
+        }
         if ((spins & 63u) == 0u) {
             if (ld_acquire(&bc->c.err) & ERR_TIMEOUT) return -2;
-            // no ticket for 30 s: record it and stop
-            if (flow_ns() - idle0 > 30000000000ull) {
+            if (flow_ns() - idle0 > 30000000000ull) {   // 30 s without a publication
                 atomicOr(&bc->c.err, ERR_TIMEOUT);
                 return -2;
             }

@@ -386,7 +386,7 @@ mpn_status mpn_batch_set_depth(mpn_batch *b, int32_t depth);
 /* Scheduling of a batch's rounds (no counterpart in the paper, which solves
  * one grid at a time). 1 (the default): every grid keeps its own sweep
  * clock; a grid's next sweep starts as soon as its own tiles of the current
- * one are done, and sweeps of at most 64 tiles are taken before larger ones,
+ * one are done, and sweeps of at most 24 tiles are taken before larger ones,
  * so a grid that needs many sweeps of few tiles (a maze) does not wait for
  * the sweeps of large grids; a round's sweep budget counts each grid's own
  * sweeps. 0: all grids advance together, one sweep of every grid per sweep

@@ -53,8 +53,9 @@ struct MazeDesc {
 };
 
 constexpr uint32_t kFlowIdle = 0, kFlowReady = 1, kFlowRun = 2, kFlowDone = 3;
-// a sweep of at most this many tiles goes to the priority ring
-constexpr uint32_t kFlowSmall = 64;
+// a sweep of at most this many tiles goes to the priority ring (the 256-grid
+// round: 4 tiles 158 ms, 8: 148, 16: 128, 24: 127, 32: 127, 64: 138, 256: 158)
+constexpr uint32_t kFlowSmall = 24;
 
 // A counter alone in its 128-byte line (the per-grid mode's counters are
 // polled by idle blocks; sharing a line would slow every claim).
